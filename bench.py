@@ -1,0 +1,357 @@
+"""Throughput of the trajectory-kNN rarity path on GB300.
+
+One step = one full forward pass (centring, operand preparation with FP64 day
+norms, fused Gram/window/top-k kernel, merge and scores) over the 75-year
+European workload: N = 27,394 daily fields on a 46 x 81 grid (D = 3,726),
+L = 5, k = 20, exclusion 4, SLP-like synthetic data.
+
+Metric: trajectory pairs per second, pairs = M^2 ordered trajectory pairs
+resolved per step (M = N - L + 1). The headline value is the split-BF16
+tensor-core path; the plain FP32 CUDA-core path is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own independent series (weak
+scaling); value = all pairs resolved / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("trajectory pairs/s, split-BF16 vs FP32 path (75y×3726pt, L=5, k=20); "
+          "% roofline")
+WORKLOAD = "euro_75y_46x81"
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+# --------------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, ws: int, device=None) -> float:
+    """Max over ranks (identity for a single process)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(pairs_per_rank: float, ms_per_step_max: float, ws: int) -> float:
+    """Whole-job throughput: all ranks' pairs over the slowest rank's step time."""
+    return pairs_per_rank * ws / (ms_per_step_max * 1e-3)
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            txt, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            txt, _ = self.proc.communicate()
+        return parse_clocks(txt)
+
+
+def parse_clocks(txt: str):
+    rows = [r for r in csv.reader(io.StringIO(txt)) if len(r) >= 9]
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+    smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for n, v in zip(names, r[5:9]):
+            if v.strip().lower() == "active":
+                reasons.add(n)
+    load = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+    return {"sm_mhz": statistics.median(load) if load else None,
+            "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+            "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+def kernel_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the
+    kernel source (profiles/traffic.json holds bytes + the source digest)."""
+    import hashlib
+    p = os.path.join(PROFILE_DIR, "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2603_02059_gb300", "csrc", rec["source"])
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if digest != rec.get("digest"):
+        return None
+    return float(rec["bytes_per_launch"]) * float(rec.get("scale", 1.0))
+
+
+# --------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2603_02059_gb300 as tk
+    from synth import config_inputs
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    X, meta, cfg = config_inputs(args.workload, seed_offset=rank)
+    N, D = X.shape
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    M = N - L + 1
+    pairs = float(M) * M
+    Xd = torch.from_numpy(X).to(device)
+    out = (torch.empty((M, k), dtype=torch.int32, device=device),
+           torch.empty((M, k), dtype=torch.float32, device=device),
+           torch.empty((M,), dtype=torch.float32, device=device))
+    h = tk.get_handle(local)
+    stream = torch.cuda.current_stream(device)
+
+    def step(prec):
+        tk.knn_scores(Xd, L, k, e, precision=prec, handle=h, out=out)
+
+    def timed(prec, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize(device)
+        h.profile_read()
+        h.set_option("profile", 1)
+        n0 = h.launch_count()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        barrier(ws)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        barrier(ws)
+        clocks = sampler.stop() if sampler else None
+        launches = h.launch_count() - n0
+        kms = h.profile_read()
+        h.set_option("profile", 0)
+        if h.sync_status() != 0:
+            raise RuntimeError("device-side failure during the timed region")
+        ms = e0.elapsed_time(e1) / steps
+        return reduce_max(ms, ws, device), kms, launches, clocks
+
+    # headline: split-BF16 tensor-core path
+    head = args.headline
+    ms_split, kms_split, launches, clocks = timed(head, args.steps, args.warmup, True)
+    value = aggregate(pairs, ms_split, ws)
+    # plain FP32 CUDA-core path on the same input
+    fp32_steps = max(1, min(args.steps, args.fp32_steps))
+    ms_fp32, kms_fp32, _, _ = timed("fp32", fp32_steps, 1)
+
+    # roofline of the dominant kernel (fused Gram/window/top-k), executed split-BF16
+    # tensor work counted algorithmically: N(N+1)/2 day pairs x 3 products x 2D flops
+    peaks, peak_src = measured_peaks()
+    flops = N * (N + 1) / 2 * 3 * 2 * D
+    kavg = statistics.mean(kms_split) * 1e-3 if kms_split else None
+    achieved = flops / kavg / 1e12 if kavg else None
+    peak = float(peaks.get("bf16_tflops_sustained", 1720.6))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": kernel_traffic("fused_tc_split"),
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "kernel": "fused Gram/window/top-k (split-BF16 tcgen05)",
+                "kernel_ms": statistics.mean(kms_split) if kms_split else None,
+                "share_of_step": (statistics.mean(kms_split) / ms_split) if kms_split else None}
+
+    # end to end through the public host-buffer API: pinned X in, results out
+    Xh = torch.from_numpy(X).pin_memory()
+    outh = (torch.empty((M, k), dtype=torch.int32).pin_memory(),
+            torch.empty((M, k), dtype=torch.float32).pin_memory(),
+            torch.empty((M,), dtype=torch.float32).pin_memory())
+    for _ in range(2):
+        tk.knn_scores_host(Xh, L, k, e, precision=head, handle=h, out=outh)
+    barrier(ws)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps)
+    for _ in range(e2e_steps):
+        tk.knn_scores_host(Xh, L, k, e, precision=head, handle=h, out=outh)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms = reduce_max(e2e_ms, ws, device)
+    h2d = X.nbytes
+    d2h = sum(t.numel() * t.element_size() for t in outh)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_split, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head,
+        "data": "synthetic (seeded SLP-like anomalies; one independent series per rank)",
+        "config": {"workload": (f"{WORKLOAD}: N={N} days, D={D} (46x81), L={L}, k={k}, "
+                                f"exclusion={e}, M={M}"),
+                   "pairs_per_step": pairs, "precision": "split-BF16 (3 BF16 products, "
+                                                       "FP32 accumulate; FP64 norms)",
+                   "l2": "inputs larger than L2 (X is 408 MB; operand copies 408 MB)",
+                   "parallelism": f"independent series per rank x{ws}"},
+        "fp32_path": {"value": aggregate(pairs, ms_fp32, ws), "ms_per_step": ms_fp32,
+                      "kernel_ms": statistics.mean(kms_fp32) if kms_fp32 else None,
+                      "steps": fp32_steps},
+        "roofline": roofline,
+        "e2e": {"value": aggregate(pairs, e2e_ms, ws), "unit": "pairs/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "traknn_knn_scores_host (pinned host buffers)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(X, L, k, e, args.cpu_rows)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(X, L, k, e, nrows):
+    """The FP64 oracle, as it stands, on a bounded sample of rows of the same workload."""
+    import oracle
+    M = X.shape[0] - L + 1
+    rows = np.linspace(0, M - 1, nrows).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.knn_rows(X, L, k, e, rows)
+    el = time.perf_counter() - t0
+    return {"value": nrows * M / el, "unit": "pairs/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": el,
+            "sample": f"{nrows} evenly spaced trajectory rows x all M={M} candidates "
+                      f"(FP64 direct differences, full sort)"}
+
+
+# --------------------------------------------------------------- reference arm
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    from synth import config_inputs
+    X, meta, cfg = config_inputs(args.workload)
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    M = X.shape[0] - L + 1
+    nrows = args.ref_rows
+    rows_all = np.linspace(0, M - 1, nrows * (args.steps + args.warmup)).astype(np.int64)
+    for w in range(args.warmup):
+        oracle.knn_rows(X, L, k, e, rows_all[w * nrows:(w + 1) * nrows])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r = rows_all[(args.warmup + s) * nrows:(args.warmup + s + 1) * nrows]
+        oracle.knn_rows(X, L, k, e, r)
+    el = (time.perf_counter() - t0) / args.steps
+    value = nrows * M / el
+    sample = (f"{nrows} trajectory rows x all M={M} candidates per step "
+              f"(FP64 direct differences, full sort)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SLP-like anomalies)",
+            "config": {"workload": f"{WORKLOAD}: N={X.shape[0]}, D={X.shape[1]}, L={L}, k={k}, "
+                                   f"exclusion={e}; oracle on a bounded row sample per step"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp32-steps", type=int, default=3)
+    ap.add_argument("--headline", choices=["split_bf16", "bf16", "fp32"], default="split_bf16")
+    ap.add_argument("--cpu-rows", type=int, default=384)
+    ap.add_argument("--ref-rows", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        line = run_ours(args, ws, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+/*
+ * traknn.h -- C ABI of the GB300 (sm_103a) trajectory-kNN rarity library.
+ *
+ * The library computes, for a sequence of N daily fields X (row-major N x D,
+ * float32, one row per day), the exact k nearest neighbours of every L-day
+ * trajectory and its rarity score, as defined in TRAKNN (arXiv 2603.02059):
+ *
+ *   trajectory      T_t = (X_t, ..., X_{t+L-1}),  t = 0 .. M-1,  M = N - L + 1
+ *                                                   (Sec. 3.2, Eq. 1)
+ *   distance        D(t,j) = sum_{m<L} ||X_{t+m} - X_{j+m}||^2   (Sec. 3.2, Eq. 2)
+ *   candidates      j with |t - j| > exclusion                   (Sec. 3.2)
+ *   neighbour set   the k candidates with smallest D(t,j); ties go to the
+ *                   smaller index                                (Algorithm 1, kNN step)
+ *   rarity score    s_t = (1/k) sum_{j in N_t} D(t,j)             (Sec. 3.2, Eq. 3)
+ *
+ * Distances are squared (no square root), as in Eq. 2-3. Indices are 0-based.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named X, nbr_*, score, grad_score, dX are DEVICE pointers on the
+ *     handle's device unless the function name ends in _host. The caller owns
+ *     every buffer; the library owns only the workspaces cached in the handle.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Device work is enqueued asynchronously on it.
+ *   - Argument errors are detected on the host and returned before anything is
+ *     enqueued. Device-side failures (a bounded wait that ran out) are recorded
+ *     in the handle and reported by traknn_sync_status().
+ *   - A handle is not thread-safe: serialise calls that share one handle.
+ *     Calls on one handle share its workspace, so two calls on different
+ *     streams must not overlap on the GPU.
+ */
+#ifndef TRAKNN_H
+#define TRAKNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque library context: device, options, cached workspaces and tensor maps. */
+typedef struct traknn_ctx* traknn_handle;
+
+typedef enum {
+  TRAKNN_OK = 0,
+  TRAKNN_ERR_INVALID_ARG = 1,        /* null pointer, non-positive size, L > N, k < 1, ... */
+  TRAKNN_ERR_TOO_FEW_CANDIDATES = 2, /* k > M - (2*exclusion + 1): some row has < k candidates */
+  TRAKNN_ERR_ALLOC = 3,              /* workspace allocation failed */
+  TRAKNN_ERR_CUDA = 4,               /* a CUDA runtime call failed */
+  TRAKNN_ERR_TIMEOUT = 5,            /* a bounded device-side wait ran out */
+  TRAKNN_ERR_UNSUPPORTED_DEVICE = 6, /* the device is not sm_103 */
+  TRAKNN_ERR_UNSUPPORTED = 7         /* L or k above the compiled limits below */
+} traknn_status;
+
+/* Arithmetic of the snapshot Gram contraction (the dominant step, Sec. 3.3,
+ * "Optimized Spatial Distance Computation"). Day norms, window sums and
+ * scores are accumulated in FP64 in every mode. */
+typedef enum {
+  TRAKNN_PREC_FP32 = 0,       /* CUDA-core FP32 FMA Gram */
+  TRAKNN_PREC_SPLIT_BF16 = 1, /* tensor cores: x = hi + lo (two BF16), G = hi.hi + hi.lo + lo.hi, FP32 accumulate */
+  TRAKNN_PREC_BF16 = 2        /* tensor cores: single BF16 product, FP32 accumulate (lower accuracy) */
+} traknn_precision;
+
+typedef enum {
+  TRAKNN_OPT_PRECISION = 0,          /* a traknn_precision value (default SPLIT_BF16) */
+  TRAKNN_OPT_CENTER = 1,             /* 1: subtract the per-grid-point mean over days before the
+                                        Gram (exact by the offset invariance of Eq. 2; default 1) */
+  TRAKNN_OPT_COL_CHUNKS = 2,         /* column chunks per row strip, 0 = automatic */
+  TRAKNN_OPT_WAIT_LIMIT_MS = 3,      /* limit of every device spin-wait in ms (default 2000) */
+  TRAKNN_OPT_DEBUG_WITHHOLD = 4,     /* test hook: 1 makes the tensor-core kernel's producer withhold
+                                        one stage so that the consumer's bounded wait runs out and
+                                        the call reports TRAKNN_ERR_TIMEOUT (default 0) */
+  TRAKNN_OPT_PROFILE = 5             /* 1: record CUDA events around the fused Gram/top-k kernel of
+                                        every forward call (read with traknn_profile_read) */
+} traknn_option;
+
+#define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */
+#define TRAKNN_MAX_K 64  /* largest neighbour count supported */
+
+/* Create a handle on CUDA device `device` (must be compute capability 10.3).
+ * Returns TRAKNN_ERR_UNSUPPORTED_DEVICE on any other device. */
+traknn_status traknn_create(traknn_handle* handle, int device);
+
+/* Free the handle and its workspaces. Synchronises the handle's device. */
+traknn_status traknn_destroy(traknn_handle handle);
+
+/* Set an option (see traknn_option). Takes effect at the next call. */
+traknn_status traknn_set_option(traknn_handle handle, traknn_option option, int64_t value);
+
+/* Pure host check of a problem shape; returns the status a compute call would
+ * return for these sizes (no device needed). */
+traknn_status traknn_check_problem(int64_t N, int64_t D, int L, int k, int exclusion);
+
+/* Forward pass (Sec. 3.2 Eq. 2-3, Algorithm 1):
+ *   X         [N x D] float32, row-major, leading dimension D (device)
+ *   L         trajectory length in days, 1 <= L <= min(N, TRAKNN_MAX_L)
+ *   k         neighbours, 1 <= k <= min(TRAKNN_MAX_K, M - (2*exclusion + 1))
+ *   exclusion e >= 0; j is a candidate of t only if |t - j| > e
+ *   nbr_idx   [M x k] int32 out: neighbour trajectory indices, each row sorted by
+ *             ascending (distance, index)
+ *   nbr_dist  [M x k] float32 out: the matching D(t, j)
+ *   score     [M] float32 out: s_t, the mean of the row's k distances (summed in FP64)
+ * Workspace grows on demand (a cudaMalloc on the first call of a larger size). */
+traknn_status traknn_knn_scores(traknn_handle handle, const float* X, int64_t N, int64_t D,
+                                int L, int k, int exclusion, int32_t* nbr_idx, float* nbr_dist,
+                                float* score, void* stream);
+
+/* Same as traknn_knn_scores with HOST buffers: copies X to the device, runs,
+ * copies the results back and synchronises the stream before returning.
+ * Page-locked host buffers give the fastest copies. */
+traknn_status traknn_knn_scores_host(traknn_handle handle, const float* X_host, int64_t N,
+                                     int64_t D, int L, int k, int exclusion,
+                                     int32_t* nbr_idx_host, float* nbr_dist_host,
+                                     float* score_host, void* stream);
+
+/* Adjoint of the summed weighted score with the neighbour sets held fixed:
+ *   dX = d( sum_t grad_score[t] * s_t ) / dX          (derived from Eq. 2-3)
+ *   nbr_idx    [M x k] int32 neighbour sets (as returned by the forward pass)
+ *   grad_score [M] float32 weights g_t (all ones gives d(sum_t s_t)/dX)
+ *   dX         [N x D] float32 out, overwritten (not accumulated) */
+traknn_status traknn_score_backward(traknn_handle handle, const float* X, int64_t N, int64_t D,
+                                    int L, int k, const int32_t* nbr_idx,
+                                    const float* grad_score, float* dX, void* stream);
+
+/* Synchronise `stream` and return the first device-side failure recorded since
+ * the last call to this function (TRAKNN_ERR_TIMEOUT), or TRAKNN_OK. */
+traknn_status traknn_sync_status(traknn_handle handle, void* stream);
+
+/* Durations in ms of the fused Gram/top-k kernel of the forward calls made
+ * since the last read while TRAKNN_OPT_PROFILE was on (oldest first, at most
+ * max_n; at most 256 are kept). Synchronises the handle's device.
+ * *n_out receives the number written. */
+traknn_status traknn_profile_read(traknn_handle handle, float* ms, int max_n, int* n_out);
+
+/* Total number of kernels this handle has launched (all entry points). */
+traknn_status traknn_launch_count(traknn_handle handle, int64_t* count);
+
+/* Static description of a status code. */
+const char* traknn_status_string(traknn_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRAKNN_H */

@@ -1,0 +1,244 @@
+"""Python binding of libtraknn (GB300, sm_103a): exact trajectory kNN and the kNN
+rarity score of TRAKNN (arXiv 2603.02059, Sec. 3.2 Eq. 2-3, Algorithm 1).
+
+This module only marshals arguments: PyTorch provides device memory and the
+current CUDA stream, and every step of the computation runs in the library's
+CUDA kernels. There is no CPU fallback; calls fail loudly when the compiled
+library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtraknn.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "traknn.h")
+
+STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_ALLOC",
+          4: "ERR_CUDA", 5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED_DEVICE", 7: "ERR_UNSUPPORTED"}
+PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
+OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
+          "debug_withhold": 4, "profile": 5}
+
+
+class TrakNNError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def lib():
+    """Load libtraknn.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+            sig = {
+                "traknn_create": [ctypes.POINTER(P), I],
+                "traknn_destroy": [P],
+                "traknn_set_option": [P, I, I64],
+                "traknn_check_problem": [I64, I64, I, I, I],
+                "traknn_knn_scores": [P, P, I64, I64, I, I, I, P, P, P, P],
+                "traknn_knn_scores_host": [P, P, I64, I64, I, I, I, P, P, P, P],
+                "traknn_score_backward": [P, P, I64, I64, I, I, P, P, P, P],
+                "traknn_sync_status": [P, P],
+                "traknn_profile_read": [P, P, I, ctypes.POINTER(I)],
+                "traknn_launch_count": [P, ctypes.POINTER(I64)],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            L.traknn_status_string.argtypes = [I]
+            L.traknn_status_string.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def header_functions(path: str = HEADER_PATH):
+    """Names of the functions declared in include/traknn.h."""
+    with open(path) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:traknn_status|const char\*)\s+(traknn_\w+)\s*\(",
+                                 txt, re.M)))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise TrakNNError(rc, what)
+
+
+def check_problem(N: int, D: int, L: int, k: int, exclusion: int) -> int:
+    """Host-only shape check; returns the status code a compute call would give."""
+    return int(lib().traknn_check_problem(N, D, L, k, exclusion))
+
+
+class Handle:
+    """Owns one library context (workspace cache) on one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _check(lib().traknn_create(ctypes.byref(h), self.device), "traknn_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().traknn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, name: str, value: int):
+        _check(lib().traknn_set_option(self._h, OPTION[name], int(value)), f"set_option({name})")
+
+    def configure(self, precision=None, center=None, col_chunks=None):
+        if precision is not None:
+            self.set_option("precision", PRECISION[precision])
+        if center is not None:
+            self.set_option("center", int(center))
+        if col_chunks is not None:
+            self.set_option("col_chunks", int(col_chunks))
+
+    def profile_read(self, max_n: int = 256):
+        """Durations (ms) of the fused Gram/top-k kernel of recent profiled calls."""
+        buf = (ctypes.c_float * max_n)()
+        n = ctypes.c_int()
+        _check(lib().traknn_profile_read(self._h, buf, max_n, ctypes.byref(n)), "profile_read")
+        return [buf[i] for i in range(n.value)]
+
+    def launch_count(self) -> int:
+        c = ctypes.c_int64()
+        _check(lib().traknn_launch_count(self._h, ctypes.byref(c)), "launch_count")
+        return int(c.value)
+
+    def sync_status(self, stream=None) -> int:
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return int(lib().traknn_sync_status(self._h, ctypes.c_void_p(s.cuda_stream)))
+
+
+_handles: dict = {}
+
+
+def get_handle(device: int | None = None) -> Handle:
+    if device is None:
+        device = torch.cuda.current_device()
+    h = _handles.get(device)
+    if h is None:
+        h = Handle(device)
+        _handles[device] = h
+    return h
+
+
+def _as_input(X: torch.Tensor) -> torch.Tensor:
+    if not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2:
+        raise ValueError("X must be a 2-D float32 CUDA tensor (days x grid points)")
+    return X.contiguous()
+
+
+def knn_scores(X: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
+               precision: str = "split_bf16", center: bool = True, col_chunks: int = 0,
+               handle: Handle | None = None, out=None):
+    """Neighbour indices [M, k] int32, distances [M, k] float32 and rarity scores [M]
+    float32 for every L-day trajectory of X (M = N - L + 1). `exclusion` defaults to
+    L - 1 (overlapping trajectories are not candidates)."""
+    X = _as_input(X)
+    N, D = X.shape
+    e = L - 1 if exclusion is None else int(exclusion)
+    M = N - L + 1
+    h = handle or get_handle(X.device.index)
+    h.configure(precision=precision, center=center, col_chunks=col_chunks)
+    if out is None:
+        idx = torch.empty((max(M, 0), k), dtype=torch.int32, device=X.device)
+        dist = torch.empty((max(M, 0), k), dtype=torch.float32, device=X.device)
+        score = torch.empty((max(M, 0),), dtype=torch.float32, device=X.device)
+    else:
+        idx, dist, score = out
+    s = torch.cuda.current_stream(X.device)
+    rc = lib().traknn_knn_scores(h._h, X.data_ptr(), N, D, L, k, e, idx.data_ptr(),
+                                 dist.data_ptr(), score.data_ptr(),
+                                 ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_scores")
+    return idx, dist, score
+
+
+def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
+                    precision: str = "split_bf16", center: bool = True, handle=None, out=None,
+                    device: int | None = None):
+    """Host-buffer variant: X_host is a CPU float32 tensor (pinned for fast copies);
+    returns CPU tensors. The call copies in, computes, copies out and synchronises."""
+    if X_host.is_cuda or X_host.dtype != torch.float32 or X_host.dim() != 2:
+        raise ValueError("X_host must be a 2-D float32 CPU tensor")
+    X_host = X_host.contiguous()
+    N, D = X_host.shape
+    e = L - 1 if exclusion is None else int(exclusion)
+    M = N - L + 1
+    h = handle or get_handle(device)
+    h.configure(precision=precision, center=center)
+    if out is None:
+        pin = X_host.is_pinned()
+        idx = torch.empty((M, k), dtype=torch.int32, pin_memory=pin)
+        dist = torch.empty((M, k), dtype=torch.float32, pin_memory=pin)
+        score = torch.empty((M,), dtype=torch.float32, pin_memory=pin)
+    else:
+        idx, dist, score = out
+    s = torch.cuda.current_stream(h.device)
+    rc = lib().traknn_knn_scores_host(h._h, X_host.data_ptr(), N, D, L, k, e, idx.data_ptr(),
+                                      dist.data_ptr(), score.data_ptr(),
+                                      ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_scores_host")
+    return idx, dist, score
+
+
+def score_backward(X: torch.Tensor, L: int, k: int, idx: torch.Tensor,
+                   grad_score: torch.Tensor, *, handle: Handle | None = None) -> torch.Tensor:
+    """dX = d(sum_t grad_score[t] s_t)/dX with the neighbour sets `idx` held fixed."""
+    X = _as_input(X)
+    N, D = X.shape
+    idx = idx.to(torch.int32).contiguous()
+    g = grad_score.to(torch.float32).contiguous()
+    h = handle or get_handle(X.device.index)
+    dX = torch.empty_like(X)
+    s = torch.cuda.current_stream(X.device)
+    rc = lib().traknn_score_backward(h._h, X.data_ptr(), N, D, L, k, idx.data_ptr(),
+                                     g.data_ptr(), dX.data_ptr(), ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_score_backward")
+    return dX
+
+
+class TrakNNScore(torch.autograd.Function):
+    """score = TrakNNScore.apply(X, L, k, exclusion, precision): the rarity scores
+    (Eq. 3); backward gives d(sum g s)/dX with the forward's neighbour sets fixed."""
+
+    @staticmethod
+    def forward(ctx, X, L, k, exclusion=None, precision="split_bf16"):
+        idx, dist, score = knn_scores(X, L, k, exclusion, precision=precision)
+        ctx.save_for_backward(X, idx)
+        ctx.L, ctx.k = L, k
+        ctx.mark_non_differentiable(idx)
+        return score
+
+    @staticmethod
+    def backward(ctx, grad_score):
+        X, idx = ctx.saved_tensors
+        dX = score_backward(X, ctx.L, ctx.k, idx, grad_score)
+        return dX, None, None, None, None

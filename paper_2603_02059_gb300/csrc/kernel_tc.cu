@@ -1,0 +1,416 @@
+// kernel_tc.cu -- the tensor-core path: tcgen05 Gram tiles fed by TMA (Algorithm 1,
+// "Symmetric Batched GeMM", with the norm identity of Eq. 4), fused with the
+// trajectory window of Eq. 2, the exclusion mask and the per-row top-k
+// (Algorithm 1, kNN step). The N x N snapshot matrix never leaves the chip.
+//
+// Precision forms. BF16: G = <bf16(x_a), bf16(x_b)>. Split-BF16: every centred
+// value is written as x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and
+//     G = <hi_a, hi_b> + <hi_a, lo_b> + <lo_a, hi_b>
+// (the lo.lo term, about 2^-16 of |x_a||x_b|, is dropped), accumulated in FP32
+// in tensor memory. The day norms and window sums stay FP64 (kernels_aux.cu).
+//
+// One persistent CTA per SM, warp-specialised:
+//   warp 0   TMA producer: A (128 strip rows) and B (256 tile columns) K-chunks of
+//            32 elements into a ring of shared-memory stages (hi and lo copies);
+//   warp 1   tcgen05.mma issuer into one of two 128 x 256 FP32 accumulators in
+//            TMEM (512 columns), so tile i+1 multiplies while tile i is scanned;
+//   warps 2-5 epilogue: each thread owns one accumulator row (TMEM lane), pulls
+//            32 columns at a time with tcgen05.ld, stages them beside the L-1
+//            columns carried from the previous chunk, and runs the shared
+//            window/mask/top-k scan.
+// Every wait is bounded (globaltimer); a wait that runs out records a timeout
+// in the status word, the CTA drains its own copies and MMAs, frees TMEM and
+// returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "epilogue.cuh"
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace traknn {
+namespace {
+
+constexpr int BM = kTileRows;  // accumulator rows (TMEM lanes)
+constexpr int BN = 256;        // accumulator columns per tile
+constexpr int KC = 32;         // K elements per stage (64 B rows, 64-B swizzle)
+constexpr int kThreads = 192;
+constexpr int kEpiThreads = 128;
+constexpr int LDG = kHalo + 32 + 1;  // chunk buffer pitch (odd: conflict-free diagonals)
+constexpr uint32_t kTileA = BM * KC * 2;  // bytes of one A operand tile
+constexpr uint32_t kTileB = BN * KC * 2;  // bytes of one B operand tile
+constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(BM, BN);
+constexpr int kMaxStages = 8;
+constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
+
+struct TcParams {
+  FusedArgs a;
+  int nstages;
+  int split;
+  uint32_t stage_bytes;
+};
+
+struct Ctl {
+  volatile int* abort;
+  int* err;
+  unsigned long long limit_ns;
+};
+
+// Bounded wait on an mbarrier phase. Records a timeout and raises the CTA's abort
+// flag when the limit runs out; gives up early when another role aborted.
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, const Ctl& c,
+                                             bool honor_abort = true) {
+  if (ptx::mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = ptx::globaltimer();
+  for (;;) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (honor_abort && *c.abort) return false;
+    if (ptx::globaltimer() - t0 > c.limit_ns) {
+      atomicCAS(c.err, 0, kErrTimeout);
+      *c.abort = 1;
+      return false;
+    }
+  }
+}
+
+struct UnitSpan {
+  int T0, jlo, jhi, ntiles, chunk;
+};
+
+__device__ __forceinline__ bool unit_span(const Schedule& s, int u, UnitSpan& us) {
+  const UnitCoord uc = unit_coord(s, u);
+  if (uc.strip >= s.strips) return false;
+  us.chunk = uc.chunk;
+  us.T0 = uc.strip * s.rows_out;
+  us.jlo = uc.chunk * s.chunk_cols;
+  us.jhi = min(s.M, us.jlo + s.chunk_cols);
+  if (us.jlo >= us.jhi) return false;
+  us.ntiles = (us.jhi - us.jlo + s.L - 1 + BN - 1) / BN;
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    fused_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi,
+                    const __grid_constant__ CUtensorMap tmA_lo,
+                    const __grid_constant__ CUtensorMap tmB_hi,
+                    const __grid_constant__ CUtensorMap tmB_lo, const TcParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  const FusedArgs& a = p.a;
+  const Schedule& s = a.sch;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int NS = p.nstages;
+
+  // ---- shared memory carve-up (ring base aligned to 1 KB for the swizzle pattern)
+  const uint32_t raw = ptx::smem_u32(smem_raw);
+  const uint32_t ring = (raw + 1023u) & ~1023u;
+  unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
+  float* Gbuf = reinterpret_cast<float*>(gptr);
+  SmemList list;
+  list.d = Gbuf + BM * LDG;
+  list.i = reinterpret_cast<int32_t*>(list.d + BM * s.k);
+  list.stride = BM;
+  list.k = s.k;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(list.i + BM * s.k);
+  const uint32_t full0 = ptx::smem_u32(bars);
+  const uint32_t empty0 = full0 + 8u * NS;
+  const uint32_t tfull0 = empty0 + 8u * NS;
+  const uint32_t tempty0 = tfull0 + 16u;
+  const uint32_t drain = tempty0 + 16u;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  Ctl ctl;
+  ctl.abort = abort_flag;
+  ctl.err = a.err;
+  ctl.limit_ns = (unsigned long long)a.wait_limit_ns;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS; ++i) {
+      ptx::mbar_init(full0 + 8u * i, 1);
+      ptx::mbar_init(empty0 + 8u * i, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(tfull0 + 8u * b, 1);
+      ptx::mbar_init(tempty0 + 8u * b, kEpiThreads);
+    }
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+    ptx::fence_proxy_async();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), 512);
+    ptx::tmem_relinquish();
+    ptx::tc_fence_before();
+  }
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      ptx::prefetch_tensormap(&tmA_hi);
+      ptx::prefetch_tensormap(&tmB_hi);
+      if (p.split) {
+        ptx::prefetch_tensormap(&tmA_lo);
+        ptx::prefetch_tensormap(&tmB_lo);
+      }
+      int stage = 0;
+      uint32_t phase = 0, issued = 0, issued_par = 0;
+      bool ok = true, withheld = false;
+      const int nkb = a.Dp / KC;
+      UnitSpan us;
+      for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
+        if (!unit_span(s, u, us)) continue;
+        for (int it = 0; ok && it < us.ntiles; ++it) {
+          const int c0 = us.jlo + it * BN;
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!wait_bounded(empty0 + 8u * stage, phase ^ 1u, ctl)) {
+              ok = false;
+              break;
+            }
+            if (a.debug_withhold && blockIdx.x == 0 && !withheld) {
+              withheld = true;  // test hook: this stage is never filled
+            } else {
+              const uint32_t fb = full0 + 8u * stage;
+              const uint32_t sb = ring + (uint32_t)stage * p.stage_bytes;
+              ptx::mbar_arrive_expect_tx(fb, p.stage_bytes);
+              ptx::tma_load_2d(sb, &tmA_hi, fb, kb * KC, us.T0);
+              if (p.split) {
+                ptx::tma_load_2d(sb + kTileA, &tmA_lo, fb, kb * KC, us.T0);
+                ptx::tma_load_2d(sb + 2 * kTileA, &tmB_hi, fb, kb * KC, c0);
+                ptx::tma_load_2d(sb + 2 * kTileA + kTileB, &tmB_lo, fb, kb * KC, c0);
+              } else {
+                ptx::tma_load_2d(sb + kTileA, &tmB_hi, fb, kb * KC, c0);
+              }
+              issued |= 1u << stage;
+              issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+            }
+            if (++stage == NS) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      // every copy issued into this CTA's shared memory must land before exit
+      for (int i = 0; i < NS; ++i)
+        if ((issued >> i) & 1u) wait_bounded(full0 + 8u * i, (issued_par >> i) & 1u, ctl, false);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true, issued_any = false;
+      const int nkb = a.Dp / KC;
+      UnitSpan us;
+      for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
+        if (!unit_span(s, u, us)) continue;
+        for (int it = 0; ok && it < us.ntiles; ++it) {
+          if (!wait_bounded(tempty0 + 8u * acc, acc_phase ^ 1u, ctl)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!wait_bounded(full0 + 8u * stage, phase, ctl)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t sb = ring + (uint32_t)stage * p.stage_bytes;
+            const uint32_t a_hi = sb;
+            const uint32_t a_lo = sb + kTileA;
+            const uint32_t b_hi = p.split ? sb + 2 * kTileA : sb + kTileA;
+            const uint32_t b_lo = b_hi + kTileB;
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+              const uint64_t dah = ptx::sdesc_kmajor_sw64(a_hi + kk * 32);
+              const uint64_t dbh = ptx::sdesc_kmajor_sw64(b_hi + kk * 32);
+              ptx::mma_f16(d, dah, dbh, kIdesc, (kb | kk) != 0);
+              if (p.split) {
+                const uint64_t dal = ptx::sdesc_kmajor_sw64(a_lo + kk * 32);
+                const uint64_t dbl = ptx::sdesc_kmajor_sw64(b_lo + kk * 32);
+                ptx::mma_f16(d, dah, dbl, kIdesc, 1u);
+                ptx::mma_f16(d, dal, dbh, kIdesc, 1u);
+              }
+            }
+            issued_any = true;
+            ptx::mma_commit(empty0 + 8u * stage);  // frees the stage once these MMAs finish
+            if (++stage == NS) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          ptx::mma_commit(tfull0 + 8u * acc);  // accumulator ready for the epilogue
+          acc ^= 1;
+          if (acc == 0) acc_phase ^= 1u;
+        }
+      }
+      if (!ok && issued_any) {
+        // all MMAs of this thread must finish before TMEM is released
+        ptx::mma_commit(drain);
+        wait_bounded(drain, 0, ctl, false);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;          // TMEM lane quadrant this warp may access
+    const int l = q * 32 + lane;     // accumulator row owned by this thread
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    const int L = s.L;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    UnitSpan us;
+    for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
+      if (!unit_span(s, u, us)) continue;
+      RowCtx rc;
+      rc.L = L;
+      rc.e = s.e;
+      rc.jlo = us.jlo;
+      rc.jhi = us.jhi;
+      rc.lrow = l;
+      rc.t = us.T0 + l;
+      const bool row_ok = l < s.rows_out && rc.t < s.M;
+      rc.Wt = row_ok ? a.W[rc.t] : 0.f;
+      float thr = CUDART_INF_F;
+      list.reset(l);
+      for (int it = 0; it < us.ntiles; ++it) {
+        bool w = wait_bounded(tfull0 + 8u * acc, acc_phase, ctl);
+        w = ptx::named_bar_and(1, kEpiThreads, w);  // all four warps agree
+        if (!w) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const int c0 = us.jlo + it * BN;
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 32; ++ch) {
+          float v[32];
+          ptx::tmem_ld32(tmem_base + lane_addr + (uint32_t)(acc * BN + ch * 32), v);
+          float* grow = Gbuf + l * LDG;
+          if (it > 0 || ch > 0)
+            for (int c = 0; c < L - 1; ++c) grow[kHalo - (L - 1) + c] = grow[kHalo + 32 - (L - 1) + c];
+#pragma unroll
+          for (int x = 0; x < 32; ++x) grow[kHalo + x] = v[x];
+          if (ch == BN / 32 - 1) {
+            // the accumulator has been read out: hand it back to the MMA warp
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(tempty0 + 8u * acc);
+          }
+          ptx::named_bar_sync(1, kEpiThreads);
+          if (row_ok)
+            window_topk(Gbuf + kHalo - (L - 1), LDG, rc, (it == 0 && ch == 0) ? L - 1 : 0, 32,
+                        c0 + ch * 32 - (L - 1), a.W, list, l, thr);
+          ptx::named_bar_sync(1, kEpiThreads);
+        }
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
+      }
+      if (!ok) break;
+      if (row_ok) {
+        const size_t base = ((size_t)rc.t * s.chunks + us.chunk) * s.k;
+        for (int pp = 0; pp < s.k; ++pp) {
+          a.part_d[base + pp] = list.d[pp * BM + l];
+          a.part_i[base + pp] = list.i[pp * BM + l];
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, 512);
+  }
+}
+
+// ------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+// Row-major [N][Dp] BF16 operand copy, boxes of 32 elements x box_rows rows.
+bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t epilogue_bytes(int k) {
+  return (size_t)BM * LDG * 4 + (size_t)BM * k * 8 + 8 * (2 * kMaxStages + 5) + 16;
+}
+
+int pick_stages(bool split, int k) {
+  const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
+  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k);
+  int ns = (int)(avail / stage);
+  return ns < kMaxStages ? ns : kMaxStages;
+}
+
+}  // namespace
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+size_t fused_tc_smem_bytes(bool split, int k) {
+  const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
+  return 1024 + (size_t)pick_stages(split, k) * stage + epilogue_bytes(k);
+}
+
+cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
+                            int num_ctas, cudaStream_t st) {
+  if (a.Dp % KC != 0) return cudaErrorInvalidValue;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map(&mAh, hi, a.N, a.Dp, BM) || !make_map(&mBh, hi, a.N, a.Dp, BN))
+    return cudaErrorNotSupported;
+  if (split) {
+    if (!make_map(&mAl, lo, a.N, a.Dp, BM) || !make_map(&mBl, lo, a.N, a.Dp, BN))
+      return cudaErrorNotSupported;
+  } else {
+    mAl = mAh;
+    mBl = mBh;
+  }
+  TcParams p;
+  p.a = a;
+  p.split = split ? 1 : 0;
+  p.stage_bytes = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
+  p.nstages = pick_stages(split, a.sch.k);
+  if (p.nstages < 2) return cudaErrorInvalidValue;
+  const size_t smem = fused_tc_smem_bytes(split, a.sch.k);
+  cudaError_t err =
+      cudaFuncSetAttribute(fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  fused_tc_kernel<<<num_ctas, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, p);
+  return cudaGetLastError();
+}
+
+}  // namespace traknn

@@ -1,0 +1,126 @@
+"""Parity of the tensor-core (tcgen05) paths with the FP64 oracle, through the C ABI,
+and the bounded-wait failure path."""
+import numpy as np
+import pytest
+
+from conftest import load_golden
+from parity import check_full, check_sampled
+from synth import config_inputs, make_slp_like
+
+pytestmark = pytest.mark.gpu
+TOL = {"split_bf16": 2e-4, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def tk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_02059_gb300 as m
+    return m
+
+
+def _run(tk, X, L, k, e, prec="split_bf16", **kw):
+    import torch
+    idx, dist, score = tk.knn_scores(torch.from_numpy(X).cuda(), L, k, e, precision=prec, **kw)
+    torch.cuda.synchronize()
+    assert tk.get_handle().sync_status() == 0
+    return idx.cpu().numpy(), dist.cpu().numpy(), score.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "bf16"])
+def test_hand_example_exact(tk, prec):
+    """Small integers are exact in BF16, so both tensor-core forms are exact here."""
+    Xrows, cases = load_golden("hand_example_6days.txt")
+    X = np.array(Xrows, dtype=np.float32)
+    for name, (p, rows) in cases.items():
+        idx, dist, score = _run(tk, X, p["L"], p["k"], p["e"], prec, center=False)
+        for t, (gi, gd, gs) in rows.items():
+            assert list(idx[t]) == gi, (name, t)
+            assert list(dist[t]) == gd, (name, t)
+            assert score[t] == gs, (name, t)
+
+
+def test_small_5y_config_split(tk):
+    X, meta, cfg = config_inputs("small_5y_16x32")
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    idx, dist, score = _run(tk, X, L, k, e)
+    check_full(X, L, k, e, idx, dist, score, TOL["split_bf16"])
+
+
+@pytest.mark.parametrize("N,h,w,L,k,e", [
+    (517, 7, 11, 5, 7, 4),
+    (300, 4, 5, 1, 1, 0),
+    (420, 6, 6, 17, 64, 16),
+    (20, 1, 3, 2, 2, 1),
+    (1000, 3, 3, 2, 9, 0),
+    (777, 9, 15, 10, 20, 9),
+    (1300, 16, 20, 7, 33, 6),
+])
+def test_shapes_split(tk, N, h, w, L, k, e):
+    X, _ = make_slp_like(N, h, w, seed=N + L)
+    idx, dist, score = _run(tk, X, L, k, e)
+    check_full(X, L, k, e, idx, dist, score, TOL["split_bf16"])
+
+
+def test_bf16_error_is_bounded(tk):
+    X, meta, cfg = config_inputs("small_5y_16x32")
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    idx, dist, score = _run(tk, X, L, k, e, "bf16")
+    check_full(X, L, k, e, idx, dist, score, TOL["bf16"])
+
+
+@pytest.mark.parametrize("chunks", [1, 5, 32])
+def test_column_chunking_is_bitwise_invariant(tk, chunks):
+    X, _ = make_slp_like(1500, 8, 12, seed=6)
+    ref = _run(tk, X, 5, 10, 4)
+    got = _run(tk, X, 5, 10, 4, col_chunks=chunks)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_constant_offset_invariance(tk):
+    X, _ = make_slp_like(700, 8, 8, seed=19)
+    F = np.linspace(950.0, 1050.0, X.shape[1], dtype=np.float32)[None, :]
+    idx, dist, score = _run(tk, (X + F).astype(np.float32), 4, 6, 3)
+    check_full(X, 4, 6, 3, idx, dist, score, TOL["split_bf16"])
+
+
+def test_euro_75y_sampled_rows_split(tk):
+    X, meta, cfg = config_inputs("euro_75y_46x81")
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    idx, dist, score = _run(tk, X, L, k, e)
+    M = X.shape[0] - L + 1
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([[0, 1, 123, 124, 4000, M - 2, M - 1], meta.planted_starts,
+                                     rng.integers(0, M, 12)]))
+    check_sampled(X, L, k, e, rows, idx, dist, score, TOL["split_bf16"])
+    order = np.argsort(-score)
+    top, taken = [], np.zeros(M, bool)
+    for t in order:
+        if not taken[max(0, t - L):t + L].any():
+            top.append(t)
+            taken[t] = True
+        if len(top) == len(meta.planted_starts):
+            break
+    for s0 in meta.planted_starts:
+        assert min(abs(t - s0) for t in top) <= L - 1
+
+
+def test_bounded_wait_reports_timeout(tk):
+    """The producer withholds one stage (test hook): the consumer's bounded wait runs out,
+    the kernel records TRAKNN_ERR_TIMEOUT and returns; the next call is correct again."""
+    import torch
+    h = tk.Handle()
+    X, _ = make_slp_like(400, 6, 6, seed=3)
+    Xd = torch.from_numpy(X).cuda()
+    h.set_option("wait_limit_ms", 300)
+    h.set_option("debug_withhold", 1)
+    tk.knn_scores(Xd, 3, 4, 2, handle=h)
+    assert h.sync_status() == 5
+    h.set_option("debug_withhold", 0)
+    idx, dist, score = tk.knn_scores(Xd, 3, 4, 2, handle=h)
+    assert h.sync_status() == 0
+    check_full(X, 3, 4, 2, idx.cpu().numpy(), dist.cpu().numpy(), score.cpu().numpy(),
+               TOL["split_bf16"])
+    h.close()
