@@ -17,6 +17,8 @@ constexpr int kMaxK = 64;
 // Status word value a kernel records when one of its bounded waits runs out
 // (matches TRAKNN_ERR_TIMEOUT of the public header).
 constexpr int kErrTimeout = 5;
+// ... and when an input it reads is out of range (TRAKNN_ERR_INVALID_ARG).
+constexpr int kErrInvalidArg = 1;
 // Column-mean partial sums use this many row slices (fixed order => deterministic).
 constexpr int kMeanSlices = 64;
 
@@ -80,6 +82,12 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Fu
                             int num_ctas, cudaStream_t st);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
                          cudaStream_t st);
+// Adjoint of the summed weighted score (kernels_adjoint.cu); `ws` must hold
+// adjoint_workspace_bytes(M, k) bytes. Adds the number of launches to *launches.
+size_t adjoint_workspace_bytes(int M, int k);
+cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int32_t* idx,
+                           const float* g, float* dX, void* ws, int* err, cudaStream_t st,
+                           int* launches);
 size_t fused_fp32_smem_bytes(int k);
 // False until the tensor-core kernel is compiled in.
 bool tc_available();

@@ -1,0 +1,176 @@
+// kernels_adjoint.cu -- gradient of the weighted summed rarity score with respect to
+// every grid-point value, the neighbour sets held fixed. From Eq. 2-3:
+//   F(X) = sum_t g_t s_t = sum_t (g_t/k) sum_{j in N_t} sum_{m<L} ||X_{t+m} - X_{j+m}||^2
+//   dF/dX_a = sum over incidences (t, j, m) with t+m = a or j+m = a of
+//             w_t (X_a - X_b),   w_t = 2 g_t / k,   b the other day of the pair.
+// The incidences of day a are
+//   forward:  t in [a-L+1, a], j in N_t,             b = j + (a - t)
+//   reverse:  j in [a-L+1, a], t with j in N_t,       b = t + (a - j)
+// Each output row is owned by one CTA that sums its incidences in a fixed order,
+// so no floating-point atomics are used and the result is bitwise reproducible.
+// The reverse lists (who has j as a neighbour) come from a counting sort whose
+// segments are then sorted by t (heap sort, one thread per segment).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace traknn {
+namespace {
+
+__global__ void adj_count_kernel(const int32_t* __restrict__ idx, int M, int k, int* count,
+                                 int* err) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)M * k) return;
+  const int j = idx[q];
+  if (j < 0 || j >= M) {
+    atomicCAS(err, 0, kErrInvalidArg);
+    return;
+  }
+  atomicAdd(count + j, 1);
+}
+
+// Exclusive scan of count[0..M) into off[0..M]; one block of 1024 threads.
+__global__ void adj_scan_kernel(const int* __restrict__ count, int M, int* off) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int per = (M + 1023) / 1024;
+  const int lo = min(M, tid * per), hi = min(M, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += count[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int run = tid > 0 ? part[tid - 1] : 0;
+  for (int i = lo; i < hi; ++i) {
+    off[i] = run;
+    run += count[i];
+  }
+  if (tid == 1023) off[M] = part[1023];
+}
+
+__global__ void adj_fill_kernel(const int32_t* __restrict__ idx, int M, int k,
+                                const int* __restrict__ off, int* cursor, int* rev) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)M * k) return;
+  const int j = idx[q];
+  if (j < 0 || j >= M) return;
+  const int t = (int)(q / k);
+  const int pos = atomicAdd(cursor + j, 1);
+  rev[off[j] + pos] = t;
+}
+
+__device__ void sift_down(int* a, int root, int n) {
+  for (;;) {
+    int c = 2 * root + 1;
+    if (c >= n) return;
+    if (c + 1 < n && a[c + 1] > a[c]) ++c;
+    if (a[root] >= a[c]) return;
+    const int tmp = a[root];
+    a[root] = a[c];
+    a[c] = tmp;
+    root = c;
+  }
+}
+
+// Sort every reverse segment ascending (heap sort: O(n log n), in place).
+__global__ void adj_sort_kernel(const int* __restrict__ off, int M, int* rev) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  int* a = rev + off[j];
+  const int n = off[j + 1] - off[j];
+  for (int r = n / 2 - 1; r >= 0; --r) sift_down(a, r, n);
+  for (int end = n - 1; end > 0; --end) {
+    const int tmp = a[0];
+    a[0] = a[end];
+    a[end] = tmp;
+    sift_down(a, 0, end);
+  }
+}
+
+constexpr int kGatherThreads = 256;
+
+// One CTA per day a: dX[a] = sum over incidences w (X[a] - X[b]), fixed order
+// (forward incidences by t then neighbour rank, then reverse ones by j then t).
+__global__ void __launch_bounds__(kGatherThreads)
+    adj_gather_kernel(const float* __restrict__ X, int N, int D, int L, int M, int k,
+                      const int32_t* __restrict__ idx, const float* __restrict__ g,
+                      const int* __restrict__ off, const int* __restrict__ rev,
+                      float* __restrict__ dX) {
+  const int a = blockIdx.x;
+  const float* xa = X + (size_t)a * D;
+  const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
+  const float inv_k2 = 2.0f / (float)k;
+  for (int p0 = 0; p0 < D; p0 += kGatherThreads * 4) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + u * kGatherThreads + threadIdx.x;
+      xv[u] = p < D ? xa[p] : 0.f;
+    }
+    for (int t = t_lo; t <= t_hi; ++t) {
+      const float w = inv_k2 * g[t];
+      for (int i = 0; i < k; ++i) {
+        const int j = idx[(size_t)t * k + i];
+        if (j < 0 || j >= M) continue;
+        const float* xb = X + (size_t)(j + a - t) * D;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int p = p0 + u * kGatherThreads + threadIdx.x;
+          if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
+        }
+      }
+    }
+    for (int j = t_lo; j <= t_hi; ++j) {
+      for (int r = off[j]; r < off[j + 1]; ++r) {
+        const int t = rev[r];
+        const float w = inv_k2 * g[t];
+        const float* xb = X + (size_t)(t + a - j) * D;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int p = p0 + u * kGatherThreads + threadIdx.x;
+          if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + u * kGatherThreads + threadIdx.x;
+      if (p < D) dX[(size_t)a * D + p] = acc[u];
+    }
+  }
+}
+
+}  // namespace
+
+size_t adjoint_workspace_bytes(int M, int k) {
+  return ((size_t)3 * M + 1 + (size_t)M * k) * sizeof(int) + 1024;
+}
+
+cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int32_t* idx,
+                           const float* g, float* dX, void* ws, int* err, cudaStream_t st,
+                           int* launches) {
+  const int M = N - L + 1;
+  int* count = static_cast<int*>(ws);
+  int* cursor = count + M;
+  int* off = cursor + M;
+  int* rev = off + M + 1;
+  cudaError_t e = cudaMemsetAsync(count, 0, (size_t)2 * M * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const long long nq = (long long)M * k;
+  const int blocks = (int)((nq + 255) / 256);
+  adj_count_kernel<<<blocks, 256, 0, st>>>(idx, M, k, count, err);
+  adj_scan_kernel<<<1, 1024, 0, st>>>(count, M, off);
+  adj_fill_kernel<<<blocks, 256, 0, st>>>(idx, M, k, off, cursor, rev);
+  adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, M, rev);
+  adj_gather_kernel<<<N, kGatherThreads, 0, st>>>(X, N, D, L, M, k, idx, g, off, rev, dX);
+  *launches += 5;
+  return cudaGetLastError();
+}
+
+}  // namespace traknn

@@ -27,6 +27,8 @@ struct traknn_ctx {
   size_t ws_bytes = 0;
   void* io = nullptr;  // device staging for the host-buffer entry point
   size_t io_bytes = 0;
+  void* adj = nullptr;  // reverse neighbour index of the adjoint
+  size_t adj_bytes = 0;
   int* err = nullptr;  // device status word
   // profiling of the fused kernel
   int profile = 0;
@@ -180,6 +182,7 @@ traknn_status traknn_destroy(traknn_handle h) {
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
   if (h->io) cudaFree(h->io);
+  if (h->adj) cudaFree(h->adj);
   if (h->err) cudaFree(h->err);
   for (int i = 0; i < traknn_ctx::kRing; ++i) {
     if (h->ev_start[i]) cudaEventDestroy(h->ev_start[i]);
@@ -325,9 +328,16 @@ traknn_status traknn_score_backward(traknn_handle h, const float* X, int64_t N, 
   if (st != TRAKNN_OK) return st;
   if (!X || !nbr_idx || !grad_score || !dX) return TRAKNN_ERR_INVALID_ARG;
   if (N < 1 || D < 1 || L < 1 || L > N || k < 1) return TRAKNN_ERR_INVALID_ARG;
+  if (N > INT_MAX / 2 || D > INT_MAX / 2) return TRAKNN_ERR_INVALID_ARG;
   if (L > TRAKNN_MAX_L || k > TRAKNN_MAX_K) return TRAKNN_ERR_UNSUPPORTED;
-  (void)stream;
-  return TRAKNN_ERR_UNSUPPORTED;
+  const int M = (int)(N - L + 1);
+  st = ensure_buffer(&h->adj, &h->adj_bytes, adjoint_workspace_bytes(M, k));
+  if (st != TRAKNN_OK) return st;
+  int launches = 0;
+  TRY_CUDA(launch_adjoint(X, (int)N, (int)D, L, k, nbr_idx, grad_score, dX, h->adj, h->err,
+                          static_cast<cudaStream_t>(stream), &launches));
+  h->launches += launches;
+  return TRAKNN_OK;
 }
 
 traknn_status traknn_sync_status(traknn_handle h, void* stream) {
