@@ -218,7 +218,10 @@ def run_ours(args, ws, rank, local):
     value = aggregate(pairs, ms_split, ws)
     # plain FP32 CUDA-core path on the same input
     fp32_steps = max(1, min(args.steps, args.fp32_steps))
-    ms_fp32, kms_fp32, _, _ = timed("fp32", fp32_steps, 1)
+    if args.skip_fp32:
+        ms_fp32, kms_fp32 = None, []
+    else:
+        ms_fp32, kms_fp32, _, _ = timed("fp32", fp32_steps, 1)
 
     # roofline of the dominant kernel (fused Gram/window/top-k), executed split-BF16
     # tensor work counted algorithmically: N(N+1)/2 day pairs x 3 products x 2D flops
@@ -236,21 +239,10 @@ def run_ours(args, ws, rank, local):
                 "share_of_step": (statistics.mean(kms_split) / ms_split) if kms_split else None}
 
     # end to end through the public host-buffer API: pinned X in, results out
-    Xh = torch.from_numpy(X).pin_memory()
-    outh = (torch.empty((M, k), dtype=torch.int32).pin_memory(),
-            torch.empty((M, k), dtype=torch.float32).pin_memory(),
-            torch.empty((M,), dtype=torch.float32).pin_memory())
-    for _ in range(2):
-        tk.knn_scores_host(Xh, L, k, e, precision=head, handle=h, out=outh)
-    barrier(ws)
-    t0 = time.perf_counter()
-    e2e_steps = max(1, args.steps)
-    for _ in range(e2e_steps):
-        tk.knn_scores_host(Xh, L, k, e, precision=head, handle=h, out=outh)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    e2e_ms = reduce_max(e2e_ms, ws, device)
-    h2d = X.nbytes
-    d2h = sum(t.numel() * t.element_size() for t in outh)
+    e2e = None
+    if not args.skip_e2e:
+        e2e = run_e2e(tk, h, X, L, k, e, head, args.steps, ws, device)
+
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
@@ -263,13 +255,11 @@ def run_ours(args, ws, rank, local):
                                                        "FP32 accumulate; FP64 norms)",
                    "l2": "inputs larger than L2 (X is 408 MB; operand copies 408 MB)",
                    "parallelism": f"independent series per rank x{ws}"},
-        "fp32_path": {"value": aggregate(pairs, ms_fp32, ws), "ms_per_step": ms_fp32,
-                      "kernel_ms": statistics.mean(kms_fp32) if kms_fp32 else None,
-                      "steps": fp32_steps},
+        "fp32_path": None if ms_fp32 is None else {
+            "value": aggregate(pairs, ms_fp32, ws), "ms_per_step": ms_fp32,
+            "kernel_ms": statistics.mean(kms_fp32) if kms_fp32 else None, "steps": fp32_steps},
         "roofline": roofline,
-        "e2e": {"value": aggregate(pairs, e2e_ms, ws), "unit": "pairs/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": "traknn_knn_scores_host (pinned host buffers)"},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -279,6 +269,30 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return line
+
+
+def run_e2e(tk, h, X, L, k, e, prec, steps, ws, device):
+    """Same metric through the host-buffer entry point: every step copies X in from
+    pinned memory, computes, copies the neighbour lists and scores out."""
+    import torch
+    M = X.shape[0] - L + 1
+    pairs = float(M) * M
+    Xh = torch.from_numpy(X).pin_memory()
+    outh = (torch.empty((M, k), dtype=torch.int32).pin_memory(),
+            torch.empty((M, k), dtype=torch.float32).pin_memory(),
+            torch.empty((M,), dtype=torch.float32).pin_memory())
+    for _ in range(2):
+        tk.knn_scores_host(Xh, L, k, e, precision=prec, handle=h, out=outh)
+    barrier(ws)
+    t0 = time.perf_counter()
+    n = max(1, steps)
+    for _ in range(n):
+        tk.knn_scores_host(Xh, L, k, e, precision=prec, handle=h, out=outh)
+    ms = reduce_max((time.perf_counter() - t0) * 1e3 / n, ws, device)
+    return {"value": aggregate(pairs, ms, ws), "unit": "pairs/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": X.nbytes,
+            "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outh),
+            "api": "traknn_knn_scores_host (pinned host buffers)"}
 
 
 def cpu_baseline(X, L, k, e, nrows):
@@ -341,6 +355,8 @@ def main(argv=None):
     ap.add_argument("--cpu-rows", type=int, default=384)
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp32", action="store_true", help="do not time the FP32 path")
+    ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
