@@ -48,7 +48,9 @@ typedef enum {
   TRAKNN_ERR_CUDA = 4,               /* a CUDA runtime call failed */
   TRAKNN_ERR_TIMEOUT = 5,            /* a bounded device-side wait ran out */
   TRAKNN_ERR_UNSUPPORTED_DEVICE = 6, /* the device is not sm_103 */
-  TRAKNN_ERR_UNSUPPORTED = 7         /* L or k above the compiled limits below */
+  TRAKNN_ERR_UNSUPPORTED = 7,        /* L or k above the compiled limits below */
+  TRAKNN_ERR_SCRATCH_LIMIT = 8       /* traknn_knn_scores_static: the problem needs more scratch
+                                        than the library's fixed device array holds */
 } traknn_status;
 
 /* Arithmetic of the snapshot Gram contraction (the dominant step, Sec. 3.3,
@@ -120,6 +122,34 @@ traknn_status traknn_knn_scores_host(traknn_handle handle, const float* X_host, 
 traknn_status traknn_score_backward(traknn_handle handle, const float* X, int64_t N, int64_t D,
                                     int L, int k, const int32_t* nbr_idx,
                                     const float* grad_score, float* dX, void* stream);
+
+/* Forward pass for callers that cannot allocate device memory. There is no
+ * counterpart in the paper: this is an interface addition of this library.
+ *
+ * Who needs it: code whose device memory belongs to another allocator or is held
+ * to a fixed budget, and code that must not cause the device-wide
+ * synchronisation a cudaMalloc or cudaFree can trigger. traknn_knn_scores needs
+ * a handle whose workspace grows by cudaMalloc; this call needs no handle and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Its scratch is one fixed 32 MiB array of device memory inside the library,
+ * which every GPU that loads the library holds until the process exits. The
+ * scratch a problem needs is about
+ *     4*N*round_up(D,32) + 260*D + 8*N + 4*M + 8*M*C*k  bytes,  C = min(8, M),
+ * plus alignment; larger problems return TRAKNN_ERR_SCRATCH_LIMIT before any
+ * work is enqueued. It runs the FP32 CUDA-core path on the current device.
+ * Arguments, layouts and outputs are those of traknn_knn_scores (X, nbr_idx,
+ * nbr_dist and score are device pointers; `stream` is a cudaStream_t).
+ *
+ * The first call on a device looks up the array's device address and caches it,
+ * which can also load the library's device code: make that first call before
+ * any stream capture. Every call reuses the same array and leaves its contents
+ * behind; nothing in it needs to be cleared by the caller. Calls that overlap on
+ * the GPU (for example on two streams without an ordering between them) race on
+ * the array and corrupt each other's results: serialise them. */
+traknn_status traknn_knn_scores_static(const float* X, int64_t N, int64_t D, int L, int k,
+                                       int exclusion, int32_t* nbr_idx, float* nbr_dist,
+                                       float* score, void* stream);
 
 /* Synchronise `stream` and return the first device-side failure recorded since
  * the last call to this function (TRAKNN_ERR_TIMEOUT), or TRAKNN_OK. */

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libtraknn.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "traknn.h")
 
 STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_ALLOC",
-          4: "ERR_CUDA", 5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED_DEVICE", 7: "ERR_UNSUPPORTED"}
+          4: "ERR_CUDA", 5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED_DEVICE", 7: "ERR_UNSUPPORTED",
+          8: "ERR_SCRATCH_LIMIT"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
           "debug_withhold": 4, "profile": 5}
@@ -57,6 +58,7 @@ def lib():
                 "traknn_sync_status": [P, P],
                 "traknn_profile_read": [P, P, I, ctypes.POINTER(I)],
                 "traknn_launch_count": [P, ctypes.POINTER(I64)],
+                "traknn_knn_scores_static": [P, I64, I64, I, I, I, P, P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -206,6 +208,26 @@ def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None 
                                       dist.data_ptr(), score.data_ptr(),
                                       ctypes.c_void_p(s.cuda_stream))
     _check(rc, "traknn_knn_scores_host")
+    return idx, dist, score
+
+
+def knn_scores_static(X: torch.Tensor, L: int, k: int, exclusion: int | None = None):
+    """FP32 forward pass that allocates no device memory inside the library: its
+    scratch is a fixed 32 MiB device array (see traknn_knn_scores_static in
+    include/traknn.h). The outputs are allocated here by torch."""
+    X = _as_input(X)
+    N, D = X.shape
+    e = L - 1 if exclusion is None else int(exclusion)
+    M = N - L + 1
+    idx = torch.empty((M, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((M, k), dtype=torch.float32, device=X.device)
+    score = torch.empty((M,), dtype=torch.float32, device=X.device)
+    s = torch.cuda.current_stream(X.device)
+    with torch.cuda.device(X.device):
+        rc = lib().traknn_knn_scores_static(X.data_ptr(), N, D, L, k, e, idx.data_ptr(),
+                                            dist.data_ptr(), score.data_ptr(),
+                                            ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_scores_static")
     return idx, dist, score
 
 

@@ -135,6 +135,7 @@ const char* traknn_status_string(traknn_status s) {
     case TRAKNN_ERR_TIMEOUT: return "a bounded device-side wait ran out";
     case TRAKNN_ERR_UNSUPPORTED_DEVICE: return "device is not sm_103";
     case TRAKNN_ERR_UNSUPPORTED: return "L or k above the compiled limits";
+    case TRAKNN_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch array of the static entry point";
   }
   return "unknown status";
 }
