@@ -44,6 +44,47 @@ constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(BM, BN);
 constexpr int kMaxStages = 8;
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
 
+// Sorted (ascending distance) list of the K best candidates of one row, held in
+// registers. Candidates arrive in increasing index order, so the strict compare
+// keeps an earlier (smaller) index ahead of an equal distance: the order is
+// (distance, index) (Algorithm 1, kNN step). K may exceed k; the first k entries
+// are then the row's k best.
+template <int K>
+struct RegList {
+  float d[K];
+  int32_t i[K];
+
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      d[p] = CUDART_INF_F;
+      i[p] = -1;
+    }
+  }
+  __device__ __forceinline__ float threshold() const { return d[K - 1]; }
+  __device__ __forceinline__ void insert(float x, int32_t xi) {
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      const bool sw = x < d[p];
+      const float td = d[p];
+      const int32_t ti = i[p];
+      d[p] = sw ? x : td;
+      i[p] = sw ? xi : ti;
+      x = sw ? td : x;
+      xi = sw ? ti : xi;
+    }
+  }
+};
+
+// Bits [lo, hi) of a 32-bit word (empty when hi <= lo).
+__device__ __forceinline__ uint32_t bit_range(int lo, int hi) {
+  lo = max(lo, 0);
+  hi = min(hi, 32);
+  if (hi <= lo) return 0u;
+  const uint32_t w = (hi - lo >= 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
+  return w << lo;
+}
+
 struct TcParams {
   FusedArgs a;
   int nstages;
@@ -90,6 +131,7 @@ __device__ __forceinline__ bool unit_span(const Schedule& s, int u, UnitSpan& us
   return true;
 }
 
+template <int K>
 __global__ void __launch_bounds__(kThreads, 1)
     fused_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                     const __grid_constant__ CUtensorMap tmA_lo,
@@ -107,12 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t ring = (raw + 1023u) & ~1023u;
   unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
   float* Gbuf = reinterpret_cast<float*>(gptr);
-  SmemList list;
-  list.d = Gbuf + BM * LDG;
-  list.i = reinterpret_cast<int32_t*>(list.d + BM * s.k);
-  list.stride = BM;
-  list.k = s.k;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(list.i + BM * s.k);
+  float* Wsh = Gbuf + BM * LDG;  // window sums of the tile's output columns
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Wsh + BN);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = full0 + 8u * NS;
   const uint32_t tfull0 = empty0 + 8u * NS;
@@ -267,23 +305,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int l = q * 32 + lane;     // accumulator row owned by this thread
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     const int L = s.L;
+    const int et = threadIdx.x - 64;  // 0..127 within the epilogue group
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
     UnitSpan us;
+    RegList<K> list;
     for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
       if (!unit_span(s, u, us)) continue;
-      RowCtx rc;
-      rc.L = L;
-      rc.e = s.e;
-      rc.jlo = us.jlo;
-      rc.jhi = us.jhi;
-      rc.lrow = l;
-      rc.t = us.T0 + l;
-      const bool row_ok = l < s.rows_out && rc.t < s.M;
-      rc.Wt = row_ok ? a.W[rc.t] : 0.f;
-      float thr = CUDART_INF_F;
-      list.reset(l);
+      const int t = us.T0 + l;
+      const bool row_ok = l < s.rows_out && t < s.M;
+      const float Wt = row_ok ? a.W[t] : 0.f;
+      list.reset();
       for (int it = 0; it < us.ntiles; ++it) {
         bool w = wait_bounded(tfull0 + 8u * acc, acc_phase, ctl);
         w = ptx::named_bar_and(1, kEpiThreads, w);  // all four warps agree
@@ -293,6 +326,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::tc_fence_after();
         const int c0 = us.jlo + it * BN;
+        // W of this tile's output columns j = c0 - (L-1) + x (the previous tile's
+        // readers finished at its last barrier)
+        for (int x = et; x < BN; x += kEpiThreads) {
+          const int j = c0 - (L - 1) + x;
+          Wsh[x] = (j >= 0 && j < s.M) ? a.W[j] : 0.f;
+        }
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32];
@@ -308,9 +347,40 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_arrive(tempty0 + 8u * acc);
           }
           ptx::named_bar_sync(1, kEpiThreads);
-          if (row_ok)
-            window_topk(Gbuf + kHalo - (L - 1), LDG, rc, (it == 0 && ch == 0) ? L - 1 : 0, 32,
-                        c0 + ch * 32 - (L - 1), a.W, list, l, thr);
+          if (row_ok) {
+            // output column x of this chunk is j = j0 + x; its window is the diagonal
+            // Gbuf[l+m][kHalo-(L-1)+x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
+            const int j0 = c0 + ch * 32 - (L - 1);
+            uint32_t valid = bit_range((it == 0 && ch == 0) ? L - 1 : 0, 32) &
+                             bit_range(us.jlo - j0, us.jhi - j0);
+            valid &= ~bit_range(t - s.e - j0, t + s.e + 1 - j0);  // exclusion zone
+            const float* g0 = Gbuf + l * LDG + kHalo - (L - 1);
+            const float* wv = Wsh + ch * 32;
+            float c[32];
+#pragma unroll
+            for (int x = 0; x < 32; ++x) c[x] = g0[x];
+            for (int m = 1; m < L; ++m) {
+              const float* gm = g0 + m * (LDG + 1);
+#pragma unroll
+              for (int x = 0; x < 32; ++x) c[x] += gm[x];
+            }
+            const float thr0 = list.threshold();
+            uint32_t cand = 0;
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+              const float dv = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);
+              cand |= (dv < thr0 ? 1u : 0u) << x;
+            }
+            cand &= valid;
+            while (cand) {
+              const int x = __ffs(cand) - 1;
+              cand &= cand - 1;
+              float cc = g0[x];
+              for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + x];
+              const float dv = fmaxf(fmaf(-2.0f, cc, Wt + wv[x]), 0.0f);
+              if (dv < list.threshold()) list.insert(dv, j0 + x);
+            }
+          }
           ptx::named_bar_sync(1, kEpiThreads);
         }
         acc ^= 1;
@@ -318,10 +388,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (row_ok) {
-        const size_t base = ((size_t)rc.t * s.chunks + us.chunk) * s.k;
-        for (int pp = 0; pp < s.k; ++pp) {
-          a.part_d[base + pp] = list.d[pp * BM + l];
-          a.part_i[base + pp] = list.i[pp * BM + l];
+        const size_t base = ((size_t)t * s.chunks + us.chunk) * s.k;
+#pragma unroll
+        for (int pp = 0; pp < K; ++pp) {
+          if (pp < s.k) {
+            a.part_d[base + pp] = list.d[pp];
+            a.part_i[base + pp] = list.i[pp];
+          }
         }
       }
     }
@@ -366,15 +439,25 @@ bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t epilogue_bytes(int k) {
-  return (size_t)BM * LDG * 4 + (size_t)BM * k * 8 + 8 * (2 * kMaxStages + 5) + 16;
-}
+size_t epilogue_bytes() { return (size_t)BM * LDG * 4 + BN * 4 + 8 * (2 * kMaxStages + 5) + 16; }
 
 int pick_stages(bool split, int k) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k);
+  (void)k;
+  const size_t avail = kSmemLimit - 1024 - epilogue_bytes();
   int ns = (int)(avail / stage);
   return ns < kMaxStages ? ns : kMaxStages;
+}
+
+template <int K>
+cudaError_t launch_k(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUtensorMap& mBh,
+                     const CUtensorMap& mBl, const TcParams& p, int num_ctas, size_t smem,
+                     cudaStream_t st) {
+  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  fused_tc_kernel<K><<<num_ctas, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, p);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -383,7 +466,7 @@ bool tc_available() { return encode_fn() != nullptr; }
 
 size_t fused_tc_smem_bytes(bool split, int k) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  return 1024 + (size_t)pick_stages(split, k) * stage + epilogue_bytes(k);
+  return 1024 + (size_t)pick_stages(split, k) * stage + epilogue_bytes();
 }
 
 cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
@@ -406,11 +489,14 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Fu
   p.nstages = pick_stages(split, a.sch.k);
   if (p.nstages < 2) return cudaErrorInvalidValue;
   const size_t smem = fused_tc_smem_bytes(split, a.sch.k);
-  cudaError_t err =
-      cudaFuncSetAttribute(fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  fused_tc_kernel<<<num_ctas, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, p);
-  return cudaGetLastError();
+  const int k = a.sch.k;
+  if (k <= 4) return launch_k<4>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 8) return launch_k<8>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 10) return launch_k<10>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 16) return launch_k<16>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 20) return launch_k<20>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 32) return launch_k<32>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  return launch_k<64>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
 }
 
 }  // namespace traknn
