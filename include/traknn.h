@@ -69,10 +69,14 @@ typedef enum {
   TRAKNN_OPT_COL_CHUNKS = 2,         /* column chunks per row strip, 0 = automatic */
   TRAKNN_OPT_WAIT_LIMIT_MS = 3,      /* limit of every device spin-wait in ms (default 2000) */
   TRAKNN_OPT_DEBUG_WITHHOLD = 4,     /* test hook: 1 makes the tensor-core kernel's producer withhold
-                                        one stage so that the consumer's bounded wait runs out and
-                                        the call reports TRAKNN_ERR_TIMEOUT (default 0) */
-  TRAKNN_OPT_PROFILE = 5             /* 1: record CUDA events around the fused Gram/top-k kernel of
+                                        the first stage of work unit 0, so that the consumer's bounded
+                                        wait runs out and the call reports TRAKNN_ERR_TIMEOUT
+                                        (default 0) */
+  TRAKNN_OPT_PROFILE = 5,            /* 1: record CUDA events around the fused Gram/top-k kernel of
                                         every forward call (read with traknn_profile_read) */
+  TRAKNN_OPT_SYMMETRIC = 6,          /* tensor-core paths: 1 evaluates each unordered pair once
+                                        (upper triangle, Sec. 3.3), 0 both triangles (default 1) */
+  TRAKNN_OPT_UNIT_COLS = 7           /* tensor-core paths: output columns per work unit, 0 = auto */
 } traknn_option;
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */

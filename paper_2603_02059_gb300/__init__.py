@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_AL
           8: "ERR_SCRATCH_LIMIT"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
-          "debug_withhold": 4, "profile": 5}
+          "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7}
 
 
 class TrakNNError(RuntimeError):
@@ -113,13 +113,18 @@ class Handle:
     def set_option(self, name: str, value: int):
         _check(lib().traknn_set_option(self._h, OPTION[name], int(value)), f"set_option({name})")
 
-    def configure(self, precision=None, center=None, col_chunks=None):
+    def configure(self, precision=None, center=None, col_chunks=None, symmetric=None,
+                  unit_cols=None):
         if precision is not None:
             self.set_option("precision", PRECISION[precision])
         if center is not None:
             self.set_option("center", int(center))
         if col_chunks is not None:
             self.set_option("col_chunks", int(col_chunks))
+        if symmetric is not None:
+            self.set_option("symmetric", int(symmetric))
+        if unit_cols is not None:
+            self.set_option("unit_cols", int(unit_cols))
 
     def profile_read(self, max_n: int = 256):
         """Durations (ms) of the fused Gram/top-k kernel of recent profiled calls."""
@@ -159,7 +164,8 @@ def _as_input(X: torch.Tensor) -> torch.Tensor:
 
 def knn_scores(X: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
                precision: str = "split_bf16", center: bool = True, col_chunks: int = 0,
-               handle: Handle | None = None, out=None):
+               symmetric: bool = True, unit_cols: int = 0, handle: Handle | None = None,
+               out=None):
     """Neighbour indices [M, k] int32, distances [M, k] float32 and rarity scores [M]
     float32 for every L-day trajectory of X (M = N - L + 1). `exclusion` defaults to
     L - 1 (overlapping trajectories are not candidates)."""
@@ -168,7 +174,8 @@ def knn_scores(X: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
     e = L - 1 if exclusion is None else int(exclusion)
     M = N - L + 1
     h = handle or get_handle(X.device.index)
-    h.configure(precision=precision, center=center, col_chunks=col_chunks)
+    h.configure(precision=precision, center=center, col_chunks=col_chunks, symmetric=symmetric,
+                unit_cols=unit_cols)
     if out is None:
         idx = torch.empty((max(M, 0), k), dtype=torch.int32, device=X.device)
         dist = torch.empty((max(M, 0), k), dtype=torch.float32, device=X.device)

@@ -52,6 +52,23 @@ struct SmemList {
     i[p * stride + tid] = jv;
     return d[(k - 1) * stride + tid];
   }
+
+  // Insert (dv, jv) in (distance, index) order when candidates arrive in any
+  // index order. Requires (dv, jv) to precede the current k-th entry.
+  __device__ __forceinline__ float insert_key(int tid, float dv, int32_t jv) const {
+    int p = k - 1;
+    while (p > 0) {
+      const float q = d[(p - 1) * stride + tid];
+      const int32_t qi = i[(p - 1) * stride + tid];
+      if (!(q > dv || (q == dv && qi > jv))) break;
+      d[p * stride + tid] = q;
+      i[p * stride + tid] = qi;
+      --p;
+    }
+    d[p * stride + tid] = dv;
+    i[p * stride + tid] = jv;
+    return d[(k - 1) * stride + tid];
+  }
 };
 
 struct RowCtx {

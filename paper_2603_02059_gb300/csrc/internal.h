@@ -67,6 +67,35 @@ struct FusedArgs {
   int debug_withhold;
 };
 
+// Work list of the tensor-core kernel. A unit is one row strip and one column
+// range; its Gram tiles are walked left to right with the diagonal carry.
+// With `sym` set only the upper triangle of the pair space is evaluated: strip s
+// covers columns j >= T0_s; inside its own block [T0_s, T0_s + rows_out) only the
+// rows collect candidates, beyond it every tile also gives each column j the
+// strip's rows as candidates (the column side), so every unordered pair is
+// evaluated once.
+struct WorkUnit {
+  int strip;  // row strip; output rows [strip*rows_out, (strip+1)*rows_out)
+  int jlo;    // first output column
+  int jhi;    // one past the last output column
+  int slot;   // slot of the row-side partial lists written by this unit
+};
+
+struct TcWork {
+  const WorkUnit* units;
+  int nunits;
+  int slots;                // row-side partial list slots per row
+  const int* slot_lo;       // [strips] first slot written for the strip's rows
+  int sym;                  // 1: upper triangle + column side
+  const long long* col_off; // [strips] first column-list of strip s (sym only)
+  float* col_d;             // [lists][k] column-side candidate distances (sorted)
+  int32_t* col_i;           // [lists][k] column-side candidate rows
+  int32_t* col_n;           // [lists] number of valid entries of each column list
+  unsigned int* thr;        // [M] bit patterns of an upper bound of each row's k-th distance
+  int* counter;             // next unit to hand out (zero before the launch)
+  int write_lists;          // 0: only publish row bounds (band pre-pass)
+};
+
 // ----------------------------------------------------------------- launchers
 cudaError_t launch_col_mean(const float* X, int N, int D, float* partial, float* mu,
                             bool center, cudaStream_t st);
@@ -79,7 +108,11 @@ cudaError_t launch_fused_fp32(const float* Xc, const FusedArgs& a, int num_ctas,
                               cudaStream_t st);
 // Tensor-core path; `split` selects the 3-product split-BF16 form.
 cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
-                            int num_ctas, cudaStream_t st);
+                            const TcWork& w, int num_ctas, cudaStream_t st);
+// Final neighbour sets of the tensor-core path: candidates of every row's partial
+// lists (and column lists) that do not exceed its bound, then an exact top-k.
+cudaError_t launch_merge_tc(const FusedArgs& a, const TcWork& w, int32_t* idx, float* dist,
+                            float* score, cudaStream_t st);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
                          cudaStream_t st);
 // Adjoint of the summed weighted score (kernels_adjoint.cu); `ws` must hold

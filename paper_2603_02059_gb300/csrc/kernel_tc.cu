@@ -76,6 +76,14 @@ struct RegList {
   }
 };
 
+// True if (d, i) would enter the column list `cl` of column c (sorted by (d, i)),
+// whose k-th distance is ct.
+__device__ __forceinline__ bool key_before(float d, int32_t i, float ct, const SmemList& cl, int c) {
+  if (d < ct) return true;
+  if (d > ct) return false;
+  return i < cl.i[(cl.k - 1) * cl.stride + c];
+}
+
 // Bits [lo, hi) of a 32-bit word (empty when hi <= lo).
 __device__ __forceinline__ uint32_t bit_range(int lo, int hi) {
   lo = max(lo, 0);
@@ -87,10 +95,13 @@ __device__ __forceinline__ uint32_t bit_range(int lo, int hi) {
 
 struct TcParams {
   FusedArgs a;
+  TcWork w;
   int nstages;
   int split;
   uint32_t stage_bytes;
 };
+
+constexpr int kColCap = 16;  // column-side candidates buffered per column and chunk
 
 struct Ctl {
   volatile int* abort;
@@ -116,20 +127,34 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, cons
 }
 
 struct UnitSpan {
-  int T0, jlo, jhi, ntiles, chunk;
+  int strip, T0, jlo, jhi, ntiles, slot;
 };
 
-__device__ __forceinline__ bool unit_span(const Schedule& s, int u, UnitSpan& us) {
-  const UnitCoord uc = unit_coord(s, u);
-  if (uc.strip >= s.strips) return false;
-  us.chunk = uc.chunk;
-  us.T0 = uc.strip * s.rows_out;
-  us.jlo = uc.chunk * s.chunk_cols;
-  us.jhi = min(s.M, us.jlo + s.chunk_cols);
+__device__ __forceinline__ bool unit_span(const Schedule& s, const TcWork& w, int u,
+                                          UnitSpan& us) {
+  const WorkUnit wu = w.units[u];
+  us.strip = wu.strip;
+  us.T0 = wu.strip * s.rows_out;
+  us.jlo = wu.jlo;
+  us.jhi = wu.jhi;
+  us.slot = wu.slot;
   if (us.jlo >= us.jhi) return false;
   us.ntiles = (us.jhi - us.jlo + s.L - 1 + BN - 1) / BN;
   return true;
 }
+
+// The k-th entry of a sorted register list (k is a run-time value, K a compile-time
+// bound): the minimum of entries k-1 .. K-1, written as a reduction so that the
+// list stays in registers.
+template <int K>
+__device__ __forceinline__ float kth_of(const RegList<K>& l, int k) {
+  float v = CUDART_INF_F;
+#pragma unroll
+  for (int p = 0; p < K; ++p) v = fminf(v, p >= k - 1 ? l.d[p] : CUDART_INF_F);
+  return v;
+}
+
+constexpr int kQueue = 4;  // depth of the per-CTA unit queue
 
 template <int K>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -140,6 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   const FusedArgs& a = p.a;
   const Schedule& s = a.sch;
+  const TcWork& w = p.w;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int NS = p.nstages;
@@ -150,14 +176,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
   float* Gbuf = reinterpret_cast<float*>(gptr);
   float* Wsh = Gbuf + BM * LDG;  // window sums of the tile's output columns
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Wsh + BN);
+  float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
+  float* Ed = Tsh + BN;          // [32][kColCap] column-side candidates: distance
+  int* Er = reinterpret_cast<int*>(Ed + 32 * kColCap);  // ... and accumulator row
+  int* ecount = Er + 32 * kColCap;  // [2][32] per-column counts, by chunk parity
+  float* Cld = reinterpret_cast<float*>(ecount + 64);  // [k][32] column-side lists
+  int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * s.k);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Cli + 32 * s.k);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = full0 + 8u * NS;
   const uint32_t tfull0 = empty0 + 8u * NS;
   const uint32_t tempty0 = tfull0 + 16u;
   const uint32_t drain = tempty0 + 16u;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
+  const uint32_t qfull0 = drain + 8u;
+  const uint32_t qempty0 = qfull0 + 8u * kQueue;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5 + 2 * kQueue);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* qval = reinterpret_cast<volatile int*>(tmem_slot + 2);  // [kQueue]
 
   Ctl ctl;
   ctl.abort = abort_flag;
@@ -174,7 +209,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::mbar_init(tempty0 + 8u * b, kEpiThreads);
     }
     ptx::mbar_init(drain, 1);
+    for (int i = 0; i < kQueue; ++i) {
+      ptx::mbar_init(qfull0 + 8u * i, 1);
+      ptx::mbar_init(qempty0 + 8u * i, 2);  // the MMA thread and the epilogue leader
+    }
     *abort_flag = 0;
+    for (int i = 0; i < 64; ++i) ecount[i] = 0;
     ptx::fence_mbar_init();
     ptx::fence_proxy_async();
   }
@@ -186,9 +226,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const int nkb = a.Dp / KC;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // Hands out units in list order (global counter) through a small queue, so the
+    // units in flight across the GPU stay a contiguous window of the list.
     if (lane == 0) {
       ptx::prefetch_tensormap(&tmA_hi);
       ptx::prefetch_tensormap(&tmB_hi);
@@ -196,13 +239,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::prefetch_tensormap(&tmA_lo);
         ptx::prefetch_tensormap(&tmB_lo);
       }
-      int stage = 0;
-      uint32_t phase = 0, issued = 0, issued_par = 0;
+      int stage = 0, qs = 0;
+      uint32_t phase = 0, qphase = 0, issued = 0, issued_par = 0;
       bool ok = true, withheld = false;
-      const int nkb = a.Dp / KC;
       UnitSpan us;
-      for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
-        if (!unit_span(s, u, us)) continue;
+      while (ok) {
+        if (!wait_bounded(qempty0 + 8u * qs, qphase ^ 1u, ctl)) break;
+        const int u = atomicAdd(w.counter, 1);
+        qval[qs] = u;
+        ptx::mbar_arrive(qfull0 + 8u * qs);
+        if (++qs == kQueue) {
+          qs = 0;
+          qphase ^= 1u;
+        }
+        if (u >= w.nunits) break;
+        if (!unit_span(s, w, u, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
           const int c0 = us.jlo + it * BN;
           for (int kb = 0; kb < nkb; ++kb) {
@@ -210,8 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               ok = false;
               break;
             }
-            if (a.debug_withhold && blockIdx.x == 0 && !withheld) {
-              withheld = true;  // test hook: this stage is never filled
+            if (a.debug_withhold && u == 0 && !withheld) {
+              withheld = true;  // test hook: unit 0's first stage is never filled
             } else {
               const uint32_t fb = full0 + 8u * stage;
               const uint32_t sb = ring + (uint32_t)stage * p.stage_bytes;
@@ -242,13 +293,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int stage = 0, acc = 0;
-      uint32_t phase = 0, acc_phase = 0;
+      int stage = 0, acc = 0, qs = 0;
+      uint32_t phase = 0, acc_phase = 0, qphase = 0;
       bool ok = true, issued_any = false;
-      const int nkb = a.Dp / KC;
       UnitSpan us;
-      for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
-        if (!unit_span(s, u, us)) continue;
+      while (ok) {
+        if (!wait_bounded(qfull0 + 8u * qs, qphase, ctl)) {
+          ok = false;
+          break;
+        }
+        const int u = qval[qs];
+        ptx::mbar_arrive(qempty0 + 8u * qs);
+        if (++qs == kQueue) {
+          qs = 0;
+          qphase ^= 1u;
+        }
+        if (u >= w.nunits) break;
+        if (!unit_span(s, w, u, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
           if (!wait_bounded(tempty0 + 8u * acc, acc_phase ^ 1u, ctl)) {
             ok = false;
@@ -306,32 +367,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     const int L = s.L;
     const int et = threadIdx.x - 64;  // 0..127 within the epilogue group
-    int acc = 0;
-    uint32_t acc_phase = 0;
+    const int cx = (warp - 2) * 8 + (lane & 7);  // column-side column of lanes 0..7
+    // the first chunk's emission counter was cleared at start-up; each chunk clears
+    // the other counter for its successor
+    int acc = 0, qs = 0, gch = 0;
+    uint32_t acc_phase = 0, qphase = 0;
     bool ok = true;
     UnitSpan us;
     RegList<K> list;
-    for (int u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
-      if (!unit_span(s, u, us)) continue;
+    SmemList cl;
+    cl.d = Cld;
+    cl.i = Cli;
+    cl.stride = 32;
+    cl.k = s.k;
+    while (ok) {
+      bool wok = wait_bounded(qfull0 + 8u * qs, qphase, ctl);
+      const int u = wok ? qval[qs] : 0;
+      wok = ptx::named_bar_and(1, kEpiThreads, wok);  // everyone has read the slot
+      if (!wok) {
+        ok = false;
+        break;
+      }
+      if (et == 0) ptx::mbar_arrive(qempty0 + 8u * qs);
+      if (++qs == kQueue) {
+        qs = 0;
+        qphase ^= 1u;
+      }
+      if (u >= w.nunits) break;
+      if (!unit_span(s, w, u, us)) continue;
       const int t = us.T0 + l;
       const bool row_ok = l < s.rows_out && t < s.M;
       const float Wt = row_ok ? a.W[t] : 0.f;
+      const int jsym = us.T0 + s.rows_out;  // column side from here on (sym)
       list.reset();
       for (int it = 0; it < us.ntiles; ++it) {
-        bool w = wait_bounded(tfull0 + 8u * acc, acc_phase, ctl);
-        w = ptx::named_bar_and(1, kEpiThreads, w);  // all four warps agree
-        if (!w) {
+        wok = wait_bounded(tfull0 + 8u * acc, acc_phase, ctl);
+        wok = ptx::named_bar_and(1, kEpiThreads, wok);  // all four warps agree
+        if (!wok) {
           ok = false;
           break;
         }
         ptx::tc_fence_after();
         const int c0 = us.jlo + it * BN;
-        // W of this tile's output columns j = c0 - (L-1) + x (the previous tile's
-        // readers finished at its last barrier)
+        // W and row bounds of this tile's output columns j = c0 - (L-1) + x (the
+        // previous tile's readers passed its last barrier)
         for (int x = et; x < BN; x += kEpiThreads) {
           const int j = c0 - (L - 1) + x;
-          Wsh[x] = (j >= 0 && j < s.M) ? a.W[j] : 0.f;
+          const bool in = j >= 0 && j < s.M;
+          Wsh[x] = in ? a.W[j] : 0.f;
+          Tsh[x] = in ? __uint_as_float(__ldcg(w.thr + j)) : 0.f;
         }
+        const float thr_row = row_ok ? __uint_as_float(__ldcg(w.thr + t)) : 0.f;
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32];
@@ -347,15 +433,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_arrive(tempty0 + 8u * acc);
           }
           ptx::named_bar_sync(1, kEpiThreads);
+          const int j0 = c0 + ch * 32 - (L - 1);
+          const int eb = gch & 1;  // emission counters of this chunk
+          // clear the next chunk's counters (their last readers passed this barrier)
+          if (et < 32) ecount[(eb ^ 1) * 32 + et] = 0;
+          // column side of this chunk: output columns j >= jsym inside the unit
+          const uint32_t colrange = w.sym ? bit_range(max(jsym, us.jlo) - j0, us.jhi - j0) &
+                                                bit_range((it == 0 && ch == 0) ? L - 1 : 0, 32)
+                                          : 0u;
+          const float thr_col = Tsh[ch * 32 + cx];
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
             // Gbuf[l+m][kHalo-(L-1)+x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
-            const int j0 = c0 + ch * 32 - (L - 1);
             uint32_t valid = bit_range((it == 0 && ch == 0) ? L - 1 : 0, 32) &
                              bit_range(us.jlo - j0, us.jhi - j0);
             valid &= ~bit_range(t - s.e - j0, t + s.e + 1 - j0);  // exclusion zone
             const float* g0 = Gbuf + l * LDG + kHalo - (L - 1);
             const float* wv = Wsh + ch * 32;
+            const float* tv = Tsh + ch * 32;
             float c[32];
 #pragma unroll
             for (int x = 0; x < 32; ++x) c[x] = g0[x];
@@ -364,31 +459,97 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int x = 0; x < 32; ++x) c[x] += gm[x];
             }
-            const float thr0 = list.threshold();
-            uint32_t cand = 0;
+            const float lthr = list.threshold();
+            uint32_t cand = 0, ccand = 0;
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
               const float dv = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);
-              cand |= (dv < thr0 ? 1u : 0u) << x;
+              cand |= (dv < lthr && dv <= thr_row ? 1u : 0u) << x;
+              ccand |= (dv <= tv[x] ? 1u : 0u) << x;
             }
             cand &= valid;
-            while (cand) {
-              const int x = __ffs(cand) - 1;
-              cand &= cand - 1;
+            ccand &= valid & colrange;
+            // recompute (identically) and hand out the few pairs that matter
+            while (cand | ccand) {
+              const uint32_t both = cand | ccand;
+              const int x = __ffs(both) - 1;
+              const uint32_t bit = 1u << x;
               float cc = g0[x];
               for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + x];
               const float dv = fmaxf(fmaf(-2.0f, cc, Wt + wv[x]), 0.0f);
-              if (dv < list.threshold()) list.insert(dv, j0 + x);
+              if ((cand & bit) && dv < list.threshold() && dv <= thr_row) list.insert(dv, j0 + x);
+              if (ccand & bit) {
+                const int pos = atomicAdd(ecount + eb * 32 + x, 1);
+                if (pos < kColCap) {
+                  Ed[x * kColCap + pos] = dv;
+                  Er[x * kColCap + pos] = l;
+                }
+              }
+              cand &= ~bit;
+              ccand &= ~bit;
             }
           }
           ptx::named_bar_sync(1, kEpiThreads);
+          // every emission of this chunk happened before the barrier; a column that
+          // overflowed its buffer is recomputed densely from the resident Gram chunk
+          const int ne_lane = ecount[eb * 32 + lane];
+          const bool dense_any = __any_sync(0xffffffffu, ne_lane > kColCap);
+          if (colrange && lane < 8 && ((colrange >> cx) & 1u)) {
+            // the column's candidates among the strip's rows, kept in (distance, row) order
+            const int j = j0 + cx;
+            const long long li = w.col_off[us.strip] + (j - jsym);
+            const int ne = ecount[eb * 32 + cx];
+            int n = 0;
+            float ct = CUDART_INF_F;
+            if (ne > 0) {
+              cl.reset(cx);
+              if (ne <= kColCap) {
+                for (int q2 = 0; q2 < ne; ++q2) {
+                  const float dv = Ed[cx * kColCap + q2];
+                  const int32_t tr = us.T0 + Er[cx * kColCap + q2];
+                  if (key_before(dv, tr, ct, cl, cx)) {
+                    ct = cl.insert_key(cx, dv, tr);
+                    ++n;
+                  }
+                }
+              } else {
+                for (int r = 0; r < s.rows_out; ++r) {
+                  const int tr = us.T0 + r;
+                  if (tr >= s.M || (tr > j ? tr - j : j - tr) <= s.e) continue;
+                  const float* g0 = Gbuf + r * LDG + kHalo - (L - 1);
+                  float cc = g0[cx];
+                  for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + cx];
+                  const float dv = fmaxf(fmaf(-2.0f, cc, a.W[tr] + Wsh[ch * 32 + cx]), 0.0f);
+                  if (dv <= thr_col && dv < ct) {
+                    ct = cl.insert(cx, dv, tr);
+                    ++n;
+                  }
+                }
+              }
+              n = min(n, s.k);
+              for (int pp = 0; pp < n; ++pp) {
+                w.col_d[li * s.k + pp] = cl.d[pp * 32 + cx];
+                w.col_i[li * s.k + pp] = cl.i[pp * 32 + cx];
+              }
+            }
+            w.col_n[li] = n;
+            if (n == s.k) atomicMin(w.thr + j, __float_as_uint(ct));
+          }
+          // the dense path read other rows' Gram values and Wsh: keep them in place
+          // until it is done (uniform: every warp saw the same counters)
+          if (dense_any) ptx::named_bar_sync(1, kEpiThreads);
+          ++gch;
         }
         acc ^= 1;
         if (acc == 0) acc_phase ^= 1u;
+        if (row_ok) {
+          const float kth = kth_of(list, s.k);
+          if (kth < thr_row) atomicMin(w.thr + t, __float_as_uint(kth));
+        }
       }
       if (!ok) break;
-      if (row_ok) {
-        const size_t base = ((size_t)t * s.chunks + us.chunk) * s.k;
+      if (row_ok && w.write_lists) {
+        const size_t base = ((size_t)t * w.slots + us.slot) * s.k;
 #pragma unroll
         for (int pp = 0; pp < K; ++pp) {
           if (pp < s.k) {
@@ -439,12 +600,14 @@ bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t epilogue_bytes() { return (size_t)BM * LDG * 4 + BN * 4 + 8 * (2 * kMaxStages + 5) + 16; }
+size_t epilogue_bytes(int k) {
+  return (size_t)BM * LDG * 4 + 2 * BN * 4 + 32 * kColCap * 8 + 64 * 4 + (size_t)32 * k * 8 +
+         8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
+}
 
 int pick_stages(bool split, int k) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  (void)k;
-  const size_t avail = kSmemLimit - 1024 - epilogue_bytes();
+  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k);
   int ns = (int)(avail / stage);
   return ns < kMaxStages ? ns : kMaxStages;
 }
@@ -466,11 +629,11 @@ bool tc_available() { return encode_fn() != nullptr; }
 
 size_t fused_tc_smem_bytes(bool split, int k) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  return 1024 + (size_t)pick_stages(split, k) * stage + epilogue_bytes();
+  return 1024 + (size_t)pick_stages(split, k) * stage + epilogue_bytes(k);
 }
 
 cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
-                            int num_ctas, cudaStream_t st) {
+                            const TcWork& w, int num_ctas, cudaStream_t st) {
   if (a.Dp % KC != 0) return cudaErrorInvalidValue;
   CUtensorMap mAh, mAl, mBh, mBl;
   if (!make_map(&mAh, hi, a.N, a.Dp, BM) || !make_map(&mBh, hi, a.N, a.Dp, BN))
@@ -484,6 +647,7 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Fu
   }
   TcParams p;
   p.a = a;
+  p.w = w;
   p.split = split ? 1 : 0;
   p.stage_bytes = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
   p.nstages = pick_stages(split, a.sch.k);

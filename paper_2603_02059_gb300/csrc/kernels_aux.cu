@@ -8,6 +8,7 @@
 #include <math_constants.h>
 
 #include <climits>
+#include <cstdint>
 
 #include "internal.h"
 
@@ -93,6 +94,51 @@ __global__ void prep_split_kernel(const float* __restrict__ X, int D, int Dp,
   if (threadIdx.x == 0) norms[a] = s;
 }
 
+// One warp per day (8 days per block): the same split as prep_split_kernel with
+// 8-byte loads and packed bf16x2 stores. Squares are formed in FP32 and summed
+// eight at a time before joining an FP64 accumulator; the partial sums carry a
+// relative rounding error of a few 1e-8, far below what the distances need.
+// Requires even D (rows of X 8-byte aligned) and Dp a multiple of 32.
+__global__ void __launch_bounds__(256)
+    prep_split_rows_kernel(const float* __restrict__ X, int N, int D, int Dp,
+                           const float* __restrict__ mu, __nv_bfloat162* __restrict__ hi,
+                           __nv_bfloat162* __restrict__ lo, double* __restrict__ norms) {
+  const int a = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= N) return;
+  const float2* x = reinterpret_cast<const float2*>(X + (size_t)a * D);
+  const float2* m2 = reinterpret_cast<const float2*>(mu);
+  __nv_bfloat162* h = hi + (size_t)a * (Dp / 2);
+  __nv_bfloat162* lw = lo + (size_t)a * (Dp / 2);
+  const int D2 = D / 2, Dp2 = Dp / 2;
+  double acc = 0.0;
+  float part = 0.f;
+  int cnt = 0;
+  for (int q = lane; q < Dp2; q += 32) {
+    float2 v = make_float2(0.f, 0.f);
+    if (q < D2) {
+      const float2 xv = x[q];
+      const float2 mv = m2[q];
+      v = make_float2(xv.x - mv.x, xv.y - mv.y);
+    }
+    const __nv_bfloat162 hv = __floats2bfloat162_rn(v.x, v.y);
+    const float2 hf = __bfloat1622float2(hv);
+    h[q] = hv;
+    lw[q] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+    part = fmaf(v.x, v.x, part);
+    part = fmaf(v.y, v.y, part);
+    if (++cnt == 4) {
+      acc += (double)part;
+      part = 0.f;
+      cnt = 0;
+    }
+  }
+  acc += (double)part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norms[a] = acc;
+}
+
 // W_t = sum_{m<L} n_{t+m}: an explicit L-term FP64 sum per trajectory.
 __global__ void window_kernel(const double* __restrict__ norms, int M, int L, float* W) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,7 +194,172 @@ __global__ void merge_kernel(const float* __restrict__ part_d, const int32_t* __
   if (lane == 0) score[t] = (float)(sum / (double)k);
 }
 
+constexpr int kMergeWarps = 8;
+constexpr int kMergeCap = 256;
+
+__device__ __forceinline__ bool key_less(float d1, int i1, float d2, int i2) {
+  return d1 < d2 || (d1 == d2 && i1 < i2);
+}
+
+// One warp per trajectory row of the tensor-core path. Every true neighbour of
+// row t has a distance <= thr[t] (an upper bound of its k-th distance taken from
+// some complete candidate list), so the candidates at or below the bound are
+// gathered from the row's partial lists and, with the symmetric work split,
+// from the column lists of the strips above; k rounds of a warp arg-min on
+// (distance, index) then give the exact neighbour set in order. If the gathered
+// set overflows the buffer, the rounds scan the lists directly.
+__global__ void __launch_bounds__(32 * kMergeWarps)
+    merge_tc_kernel(const float* __restrict__ part_d, const int32_t* __restrict__ part_i,
+                    Schedule s, TcWork w, int32_t* __restrict__ idx, float* __restrict__ dist,
+                    float* __restrict__ score) {
+  __shared__ float bd[kMergeWarps][kMergeCap];
+  __shared__ int bi[kMergeWarps][kMergeCap];
+  __shared__ int bn[kMergeWarps];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kMergeWarps + wid;
+  if (t >= s.M) return;
+  const int k = s.k;
+  const int strip = t / s.rows_out;
+  float thr = __uint_as_float(w.thr[t]);
+  const int c_lo = w.slot_lo[strip];
+  auto push = [&](float d, int i) {
+    const int pos = atomicAdd(&bn[wid], 1);
+    if (pos < kMergeCap) {
+      bd[wid][pos] = d;
+      bi[wid][pos] = i;
+    }
+  };
+  // k rounds of a warp arg-min over the buffer (strictly after the previous pick)
+  auto select = [&](int n, float* outd, int* outi) {
+    float last_d = -CUDART_INF_F;
+    int last_i = -1;
+    for (int r = 0; r < k; ++r) {
+      float best_d = CUDART_INF_F;
+      int best_i = INT_MAX;
+      for (int q = lane; q < n; q += 32) {
+        const float d = bd[wid][q];
+        const int ii = bi[wid][q];
+        if (key_less(last_d, last_i, d, ii) && key_less(d, ii, best_d, best_i)) {
+          best_d = d;
+          best_i = ii;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, best_d, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, best_i, o);
+        if (key_less(od, oi, best_d, best_i)) {
+          best_d = od;
+          best_i = oi;
+        }
+      }
+      last_d = best_d;
+      last_i = best_i;
+      if (outd) {
+        outd[r] = best_d;
+        outi[r] = best_i;
+      }
+    }
+    return last_d;
+  };
+  int n = 0;
+  for (int pass = 0; pass < 64; ++pass) {
+    if (lane == 0) bn[wid] = 0;
+    __syncwarp();
+    for (int c = c_lo + lane; c < w.slots; c += 32) {
+      const size_t b = ((size_t)t * w.slots + c) * k;
+      for (int p = 0; p < k; ++p) {
+        const int ii = part_i[b + p];
+        const float d = part_d[b + p];
+        if (ii < 0 || d > thr) break;
+        push(d, ii);
+      }
+    }
+    if (w.sym) {
+      for (int s2 = lane; s2 < strip; s2 += 32) {
+        const long long li = w.col_off[s2] + (t - (s2 + 1) * s.rows_out);
+        const int nn = w.col_n[li];
+        for (int p = 0; p < nn; ++p) {
+          const float d = w.col_d[li * k + p];
+          if (d > thr) break;
+          push(d, w.col_i[li * k + p]);
+        }
+      }
+    }
+    __syncwarp();
+    n = bn[wid];
+    __syncwarp();
+    if (n <= kMergeCap) break;
+    // overflow: the k-th smallest of the buffered (valid, distinct) candidates is a
+    // tighter bound; gather again under it
+    thr = select(kMergeCap, nullptr, nullptr);
+  }
+  // final selection, written in (distance, index) order; if ties at the bound keep
+  // the candidate set larger than the buffer, scan the lists directly each round
+  const bool direct = n > kMergeCap;
+  float last_d = -CUDART_INF_F;
+  int last_i = -1;
+  double sum = 0.0;
+  for (int r = 0; r < k; ++r) {
+    float best_d = CUDART_INF_F;
+    int best_i = INT_MAX;
+    auto consider = [&](float d, int ii) {
+      if (key_less(last_d, last_i, d, ii) && key_less(d, ii, best_d, best_i)) {
+        best_d = d;
+        best_i = ii;
+      }
+    };
+    if (!direct) {
+      for (int q = lane; q < n; q += 32) consider(bd[wid][q], bi[wid][q]);
+    } else {
+      for (int c = c_lo + lane; c < w.slots; c += 32) {
+        const size_t b = ((size_t)t * w.slots + c) * k;
+        for (int p = 0; p < k; ++p) {
+          const int ii = part_i[b + p];
+          if (ii < 0 || part_d[b + p] > thr) break;
+          consider(part_d[b + p], ii);
+        }
+      }
+      if (w.sym) {
+        for (int s2 = lane; s2 < strip; s2 += 32) {
+          const long long li = w.col_off[s2] + (t - (s2 + 1) * s.rows_out);
+          const int nn = w.col_n[li];
+          for (int p = 0; p < nn; ++p) {
+            if (w.col_d[li * k + p] > thr) break;
+            consider(w.col_d[li * k + p], w.col_i[li * k + p]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float od2 = __shfl_xor_sync(0xffffffffu, best_d, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, best_i, o);
+      if (key_less(od2, oi, best_d, best_i)) {
+        best_d = od2;
+        best_i = oi;
+      }
+    }
+    last_d = best_d;
+    last_i = best_i;
+    if (lane == 0) {
+      idx[(size_t)t * k + r] = best_i == INT_MAX ? -1 : best_i;
+      dist[(size_t)t * k + r] = best_d;
+      sum += (double)best_d;
+    }
+  }
+  if (lane == 0) score[t] = (float)(sum / (double)k);
+}
+
 }  // namespace
+
+cudaError_t launch_merge_tc(const FusedArgs& a, const TcWork& w, int32_t* idx, float* dist,
+                            float* score, cudaStream_t st) {
+  const int blocks = (a.sch.M + kMergeWarps - 1) / kMergeWarps;
+  merge_tc_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(a.part_d, a.part_i, a.sch, w, idx, dist,
+                                                       score);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_col_mean(const float* X, int N, int D, float* partial, float* mu, bool center,
                             cudaStream_t st) {
@@ -166,8 +377,13 @@ cudaError_t launch_prep_fp32(const float* X, int N, int D, int Dp, const float* 
 
 cudaError_t launch_prep_split(const float* X, int N, int D, int Dp, const float* mu, void* hi,
                               void* lo, double* norms, cudaStream_t st) {
-  prep_split_kernel<<<N, 256, 0, st>>>(X, D, Dp, mu, static_cast<__nv_bfloat16*>(hi),
-                                       static_cast<__nv_bfloat16*>(lo), norms);
+  const bool vec = (D % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 8 == 0);
+  if (vec)
+    prep_split_rows_kernel<<<(N + 7) / 8, 256, 0, st>>>(
+        X, N, D, Dp, mu, static_cast<__nv_bfloat162*>(hi), static_cast<__nv_bfloat162*>(lo), norms);
+  else
+    prep_split_kernel<<<N, 256, 0, st>>>(X, D, Dp, mu, static_cast<__nv_bfloat16*>(hi),
+                                         static_cast<__nv_bfloat16*>(lo), norms);
   return cudaGetLastError();
 }
 

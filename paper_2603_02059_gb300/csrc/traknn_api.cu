@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/traknn.h"
 #include "internal.h"
@@ -37,6 +38,17 @@ struct traknn_ctx {
   cudaEvent_t ev_stop[kRing] = {};
   int ev_head = 0, ev_count = 0;
   int64_t launches = 0;
+  // tensor-core work split
+  int sym = 1;
+  int unit_cols = 0;
+  struct {
+    int M = -1, L = -1, k = -1, e = -1, sym = -1, cols = -1;
+    int strips = 0, slots = 0, nunits = 0, nband = 0;
+    long long col_lists = 0;
+    size_t bytes = 0;
+  } plan;
+  void* plan_dev = nullptr;  // units, col_off, slot_lo
+  size_t plan_dev_bytes = 0;
 };
 
 namespace {
@@ -115,6 +127,66 @@ Layout make_layout(int64_t N, int64_t D, const Schedule& s) {
   return l;
 }
 
+// Tensor-core work list. Units (strip, column range) are ordered in groups of
+// strips that run side by side (sharing A and B tiles in L2); with the symmetric
+// split the groups go from the last strip upwards, so the rows whose own lists
+// bound the column side of a strip have mostly been processed before it.
+static_assert(sizeof(WorkUnit) == 16, "work unit layout");
+
+struct TcPlan {
+  std::vector<WorkUnit> units;
+  std::vector<WorkUnit> band;  // threshold pre-pass: one unit around each strip's diagonal
+  std::vector<long long> col_off;
+  std::vector<int> slot_lo;
+  int strips = 0, slots = 0;
+  long long col_lists = 0;
+};
+
+TcPlan make_tc_plan(int M, int L, int sym, int cols_opt, int sm_count) {
+  TcPlan p;
+  const int R = kTileRows - (L - 1);
+  p.strips = (M + R - 1) / R;
+  // a unit of n whole 256-column tiles covers 256 n - (L-1) output columns
+  const int cols = cols_opt > 0 ? cols_opt : 8 * 256 - (L - 1);
+  p.slots = (M + cols - 1) / cols;
+  const int group = std::max(1, std::min(p.strips, 19));
+  (void)sm_count;
+  p.col_off.resize(p.strips);
+  p.slot_lo.resize(p.strips);
+  long long off = 0;
+  for (int s = 0; s < p.strips; ++s) {
+    p.col_off[s] = off;
+    const long long first_col = (long long)(s + 1) * R;  // column side starts here
+    if (sym && first_col < M) off += M - first_col;
+    p.slot_lo[s] = sym ? (s * R) / cols : 0;
+  }
+  p.col_lists = off;
+  const int ngroups = (p.strips + group - 1) / group;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const int g = sym ? ngroups - 1 - gi : gi;
+    const int s_lo = g * group, s_hi = std::min(p.strips, s_lo + group);
+    for (int c = 0; c < p.slots; ++c)
+      for (int s = s_lo; s < s_hi; ++s) {
+        const int T0 = s * R;
+        int jlo = c * cols;
+        const int jhi = std::min(M, (c + 1) * cols);
+        if (sym) jlo = std::max(jlo, T0);
+        if (jlo >= jhi) continue;
+        p.units.push_back(WorkUnit{s, jlo, jhi, c});
+      }
+  }
+  // Band pre-pass: two tiles of columns centred on each strip's own rows. Its
+  // row-side lists are not kept; their k-th distances seed the row bounds that
+  // prune both sides of the main pass (candidates near in time first).
+  const int bw = std::max(0, (2 * 256 - (L - 1) - R) / 2);
+  for (int s = 0; s < p.strips; ++s) {
+    const int T0 = s * R;
+    const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
+    if (jlo < jhi) p.band.push_back(WorkUnit{s, jlo, jhi, 0});
+  }
+  return p;
+}
+
 traknn_status check_handle(traknn_handle h) {
   if (!h) return TRAKNN_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return TRAKNN_ERR_CUDA;
@@ -184,6 +256,7 @@ traknn_status traknn_destroy(traknn_handle h) {
   if (h->ws) cudaFree(h->ws);
   if (h->io) cudaFree(h->io);
   if (h->adj) cudaFree(h->adj);
+  if (h->plan_dev) cudaFree(h->plan_dev);
   if (h->err) cudaFree(h->err);
   for (int i = 0; i < traknn_ctx::kRing; ++i) {
     if (h->ev_start[i]) cudaEventDestroy(h->ev_start[i]);
@@ -214,6 +287,13 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
     case TRAKNN_OPT_DEBUG_WITHHOLD:
       h->debug_withhold = v ? 1 : 0;
       return TRAKNN_OK;
+    case TRAKNN_OPT_SYMMETRIC:
+      h->sym = v ? 1 : 0;
+      return TRAKNN_OK;
+    case TRAKNN_OPT_UNIT_COLS:
+      if (v < 0 || v > (1 << 24)) return TRAKNN_ERR_INVALID_ARG;
+      h->unit_cols = (int)v;
+      return TRAKNN_OK;
     case TRAKNN_OPT_PROFILE:
       if (v && !h->ev_start[0]) {
         if (cudaSetDevice(h->device) != cudaSuccess) return TRAKNN_ERR_CUDA;
@@ -240,8 +320,60 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int M = (int)(N - L + 1);
 
-  const Schedule sch = make_schedule(M, L, k, e, h->sm_count, h->col_chunks);
-  const Layout lay = make_layout(N, D, sch);
+  const bool tc = h->precision != TRAKNN_PREC_FP32;
+  if (tc && !tc_available()) return TRAKNN_ERR_UNSUPPORTED;
+  Schedule sch = make_schedule(M, L, k, e, h->sm_count, h->col_chunks);
+
+  // tensor-core work list (rebuilt when the shape changes)
+  auto& pl = h->plan;
+  if (tc && (pl.M != M || pl.L != L || pl.k != k || pl.e != e || pl.sym != h->sym ||
+             pl.cols != h->unit_cols)) {
+    TcPlan tp = make_tc_plan(M, L, h->sym, h->unit_cols, h->sm_count);
+    const size_t nb = tp.band.size();
+    tp.units.insert(tp.units.end(), tp.band.begin(), tp.band.end());  // band units last
+    const size_t ub = align_up(tp.units.size() * sizeof(WorkUnit), 256);
+    const size_t cb = align_up(tp.col_off.size() * sizeof(long long), 256);
+    const size_t sb = align_up(tp.slot_lo.size() * sizeof(int), 256);
+    if (h->plan_dev && h->plan_dev_bytes < ub + cb + sb) TRY_CUDA(cudaStreamSynchronize(s));
+    st = ensure_buffer(&h->plan_dev, &h->plan_dev_bytes, ub + cb + sb);
+    if (st != TRAKNN_OK) return st;
+    char* pd = static_cast<char*>(h->plan_dev);
+    TRY_CUDA(cudaMemcpyAsync(pd, tp.units.data(), tp.units.size() * sizeof(WorkUnit),
+                             cudaMemcpyHostToDevice, s));
+    TRY_CUDA(cudaMemcpyAsync(pd + ub, tp.col_off.data(), tp.col_off.size() * sizeof(long long),
+                             cudaMemcpyHostToDevice, s));
+    TRY_CUDA(cudaMemcpyAsync(pd + ub + cb, tp.slot_lo.data(), tp.slot_lo.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, s));
+    pl.M = M;
+    pl.L = L;
+    pl.k = k;
+    pl.e = e;
+    pl.sym = h->sym;
+    pl.cols = h->unit_cols;
+    pl.strips = tp.strips;
+    pl.slots = tp.slots;
+    pl.nunits = (int)(tp.units.size() - nb);
+    pl.nband = (int)nb;
+    pl.col_lists = tp.col_lists;
+    pl.bytes = ub;  // device layout: units | col_off | slot_lo
+  }
+  if (tc) sch.chunks = pl.slots;  // partial lists: one slot per column range
+
+  Layout lay = make_layout(N, D, sch);
+  size_t thr_off = 0, coln_off = 0, cold_off = 0, coli_off = 0, cnt_off = 0;
+  if (tc) {
+    auto take = [&](size_t bytes) {
+      lay.total = align_up(lay.total, 256);
+      size_t o = lay.total;
+      lay.total += bytes;
+      return o;
+    };
+    thr_off = take((size_t)M * sizeof(unsigned int));
+    coln_off = take((size_t)pl.col_lists * sizeof(int32_t));
+    cold_off = take((size_t)pl.col_lists * k * sizeof(float));
+    coli_off = take((size_t)pl.col_lists * k * sizeof(int32_t));
+    cnt_off = take(256);
+  }
   st = ensure_buffer(&h->ws, &h->ws_bytes, lay.total);
   if (st != TRAKNN_OK) return st;
   char* ws = static_cast<char*>(h->ws);
@@ -262,28 +394,66 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   fa.wait_limit_ns = (long long)h->wait_limit_ms * 1000000LL;
   fa.debug_withhold = h->debug_withhold;
 
-  if (h->precision != TRAKNN_PREC_FP32 && !tc_available()) return TRAKNN_ERR_UNSUPPORTED;
+  TcWork tw;
+  if (tc) {
+    char* pd = static_cast<char*>(h->plan_dev);
+    const size_t ub = pl.bytes;
+    const size_t cb = align_up((size_t)pl.strips * sizeof(long long), 256);
+    tw.units = reinterpret_cast<const WorkUnit*>(pd);
+    tw.nunits = pl.nunits;
+    tw.slots = pl.slots;
+    tw.col_off = reinterpret_cast<const long long*>(pd + ub);
+    tw.slot_lo = reinterpret_cast<const int*>(pd + ub + cb);
+    tw.sym = h->sym;
+    tw.thr = reinterpret_cast<unsigned int*>(ws + thr_off);
+    tw.col_n = reinterpret_cast<int32_t*>(ws + coln_off);
+    tw.col_d = reinterpret_cast<float*>(ws + cold_off);
+    tw.col_i = reinterpret_cast<int32_t*>(ws + coli_off);
+    tw.counter = reinterpret_cast<int*>(ws + cnt_off);
+    tw.write_lists = 1;
+  }
+
   TRY_CUDA(launch_col_mean(X, (int)N, (int)D, partial, mu, h->center != 0, s));
   h->launches += h->center ? 2 : 1;
   const int slot = h->ev_head;
   void* hi = ops;
   void* lo = static_cast<char*>(ops) + (size_t)N * lay.Dp * 2;
-  if (h->precision == TRAKNN_PREC_FP32)
+  if (!tc)
     TRY_CUDA(launch_prep_fp32(X, (int)N, (int)D, lay.Dp, mu, static_cast<float*>(ops), norms, s));
   else
     TRY_CUDA(launch_prep_split(X, (int)N, (int)D, lay.Dp, mu, hi, lo, norms, s));
   TRY_CUDA(launch_window(norms, M, L, W, s));
+  if (tc) {
+    TRY_CUDA(cudaMemsetAsync(tw.thr, 0x7F, (size_t)M * sizeof(unsigned int), s));
+    TRY_CUDA(cudaMemsetAsync(tw.counter, 0, 2 * sizeof(int), s));
+  }
   if (h->profile) TRY_CUDA(cudaEventRecord(h->ev_start[slot], s));
-  if (h->precision == TRAKNN_PREC_FP32)
+  if (!tc) {
     TRY_CUDA(launch_fused_fp32(static_cast<float*>(ops), fa, h->sm_count, s));
-  else
-    TRY_CUDA(launch_fused_tc(hi, lo, h->precision == TRAKNN_PREC_SPLIT_BF16, fa, h->sm_count, s));
+  } else {
+    const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
+    if (pl.nband > 0) {
+      // threshold pre-pass over the band units (stored after the main units)
+      TcWork bw = tw;
+      bw.units = tw.units + pl.nunits;
+      bw.nunits = pl.nband;
+      bw.sym = 0;
+      bw.write_lists = 0;
+      bw.counter = tw.counter + 1;
+      TRY_CUDA(launch_fused_tc(hi, lo, split, fa, bw, h->sm_count, s));
+      h->launches += 1;
+    }
+    TRY_CUDA(launch_fused_tc(hi, lo, split, fa, tw, h->sm_count, s));
+  }
   if (h->profile) {
     TRY_CUDA(cudaEventRecord(h->ev_stop[slot], s));
     h->ev_head = (h->ev_head + 1) % traknn_ctx::kRing;
     h->ev_count = std::min(h->ev_count + 1, traknn_ctx::kRing);
   }
-  TRY_CUDA(launch_merge(fa, nbr_idx, nbr_dist, score, s));
+  if (!tc)
+    TRY_CUDA(launch_merge(fa, nbr_idx, nbr_dist, score, s));
+  else
+    TRY_CUDA(launch_merge_tc(fa, tw, nbr_idx, nbr_dist, score, s));
   h->launches += 4;
   return TRAKNN_OK;
 }

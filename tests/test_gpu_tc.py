@@ -70,13 +70,36 @@ def test_bf16_error_is_bounded(tk):
     check_full(X, L, k, e, idx, dist, score, TOL["bf16"])
 
 
-@pytest.mark.parametrize("chunks", [1, 5, 32])
-def test_column_chunking_is_bitwise_invariant(tk, chunks):
+@pytest.mark.parametrize("cols", [256, 300, 700, 5000])
+def test_work_unit_size_is_bitwise_invariant(tk, cols):
     X, _ = make_slp_like(1500, 8, 12, seed=6)
     ref = _run(tk, X, 5, 10, 4)
-    got = _run(tk, X, 5, 10, 4, col_chunks=chunks)
+    got = _run(tk, X, 5, 10, 4, unit_cols=cols)
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("N,h,w,L,k,e", [(1500, 8, 12, 5, 10, 4), (777, 9, 15, 10, 20, 9),
+                                         (420, 6, 6, 17, 64, 16), (300, 4, 5, 1, 1, 0),
+                                         (1000, 3, 3, 2, 9, 0)])
+def test_symmetric_split_equals_full_evaluation(tk, N, h, w, L, k, e):
+    """Evaluating each unordered pair once (upper triangle with column-side lists)
+    gives the neighbour lists and scores of evaluating both triangles. D(t,j) and
+    D(j,t) come from Gram tiles with the operand roles swapped, so they may differ
+    in the last bit: distances agree to 1e-6 and index sets may differ only at
+    near ties."""
+    X, _ = make_slp_like(N, h, w, seed=N + 2 * L)
+    full = _run(tk, X, L, k, e, symmetric=False)
+    half = _run(tk, X, L, k, e, symmetric=True)
+    rel = np.abs(full[1] - half[1]) / np.maximum(np.abs(full[1]), 1e-30)
+    assert rel.max() <= 1e-6
+    assert np.allclose(full[2], half[2], rtol=1e-6)
+    same = (full[0] == half[0]).all(axis=1)
+    near = np.abs(full[1][:, -1] - full[1][:, 0]) >= 0  # rows that differ must be near ties
+    for t in np.nonzero(~same)[0]:
+        diff = set(full[0][t]) ^ set(half[0][t])
+        assert np.all(np.abs(half[1][t][-1] - full[1][t][-1]) <= 1e-6 * full[1][t][-1]), t
+        assert len(diff) <= 2 * k and near[t]
 
 
 def test_constant_offset_invariance(tk):
@@ -124,3 +147,17 @@ def test_bounded_wait_reports_timeout(tk):
     check_full(X, 3, 4, 2, idx.cpu().numpy(), dist.cpu().numpy(), score.cpu().numpy(),
                TOL["split_bf16"])
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_constant_series_ties_go_to_smaller_indices(tk, prec):
+    """Every distance is zero: each row's neighbours are its k smallest candidate
+    indices (Algorithm 1's kNN step with the smaller-index tie rule)."""
+    N, L, k, e = 700, 3, 12, 2
+    X = np.full((N, 10), 3.25, dtype=np.float32)
+    idx, dist, score = _run(tk, X, L, k, e, prec)
+    M = N - L + 1
+    for t in range(M):
+        exp = [j for j in range(M) if abs(j - t) > e][:k]
+        assert list(idx[t]) == exp, t
+    assert np.all(dist == 0) and np.all(score == 0)
