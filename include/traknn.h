@@ -76,7 +76,8 @@ typedef enum {
                                         every forward call (read with traknn_profile_read) */
   TRAKNN_OPT_SYMMETRIC = 6,          /* tensor-core paths: 1 evaluates each unordered pair once
                                         (upper triangle, Sec. 3.3), 0 both triangles (default 1) */
-  TRAKNN_OPT_UNIT_COLS = 7           /* tensor-core paths: output columns per work unit, 0 = auto */
+  TRAKNN_OPT_UNIT_COLS = 7,          /* tensor-core paths: output columns per work unit, 0 = auto */
+  TRAKNN_OPT_STATS = 8               /* 1: count kernel events (read with traknn_stats_read) */
 } traknn_option;
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */
@@ -164,6 +165,14 @@ traknn_status traknn_sync_status(traknn_handle handle, void* stream);
  * max_n; at most 256 are kept). Synchronises the handle's device.
  * *n_out receives the number written. */
 traknn_status traknn_profile_read(traknn_handle handle, float* ms, int max_n, int* n_out);
+
+/* Event counters of the tensor-core kernel accumulated while TRAKNN_OPT_STATS was on
+ * (diagnostics): [0] row-side list insertions, [1] column-side candidates,
+ * [2] columns recomputed after a buffer overflow, [3] non-empty column lists,
+ * [4] 32-column chunks processed, [5] MMA-thread cycles waiting for a free
+ * accumulator, [6] MMA-thread cycles waiting for operands, [7] MMA-thread cycles
+ * in total (all summed over CTAs). Synchronises the device and resets them. */
+traknn_status traknn_stats_read(traknn_handle handle, uint64_t* counters, int n);
 
 /* Total number of kernels this handle has launched (all entry points). */
 traknn_status traknn_launch_count(traknn_handle handle, int64_t* count);

@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_AL
           8: "ERR_SCRATCH_LIMIT"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
-          "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7}
+          "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7, "stats": 8}
 
 
 class TrakNNError(RuntimeError):
@@ -59,6 +59,7 @@ def lib():
                 "traknn_profile_read": [P, P, I, ctypes.POINTER(I)],
                 "traknn_launch_count": [P, ctypes.POINTER(I64)],
                 "traknn_knn_scores_static": [P, I64, I64, I, I, I, P, P, P, P],
+                "traknn_stats_read": [P, P, I],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -132,6 +133,14 @@ class Handle:
         n = ctypes.c_int()
         _check(lib().traknn_profile_read(self._h, buf, max_n, ctypes.byref(n)), "profile_read")
         return [buf[i] for i in range(n.value)]
+
+    def stats_read(self):
+        """Kernel event counters since the last read (TRAKNN_OPT_STATS)."""
+        buf = (ctypes.c_uint64 * 8)()
+        _check(lib().traknn_stats_read(self._h, buf, 8), "stats_read")
+        names = ["row_inserts", "col_emits", "col_dense", "col_lists", "chunks",
+                 "mma_wait_tmem", "mma_wait_full", "mma_cycles"]
+        return {n: int(buf[i]) for i, n in enumerate(names)}
 
     def launch_count(self) -> int:
         c = ctypes.c_int64()

@@ -94,6 +94,20 @@ struct TcWork {
   unsigned int* thr;        // [M] bit patterns of an upper bound of each row's k-th distance
   int* counter;             // next unit to hand out (zero before the launch)
   int write_lists;          // 0: only publish row bounds (band pre-pass)
+  unsigned long long* stats;  // optional event counters (see kStat*), nullptr = off
+};
+
+// Event counters of the tensor-core kernel (diagnostics, TRAKNN_OPT_STATS).
+enum : int {
+  kStatRowInserts = 0,     // row-side list insertions
+  kStatColEmits = 1,       // column-side candidates handed to a column
+  kStatColDense = 2,       // columns recomputed densely after a buffer overflow
+  kStatColLists = 3,       // non-empty column lists written
+  kStatChunks = 4,         // 32-column chunks processed
+  kStatMmaWaitTmem = 5,    // MMA-thread cycles spent waiting for a free accumulator
+  kStatMmaWaitFull = 6,    // MMA-thread cycles spent waiting for a filled stage
+  kStatMmaCycles = 7,      // MMA-thread cycles from start to end, summed over CTAs
+  kStatCount = 8
 };
 
 // ----------------------------------------------------------------- launchers
@@ -124,6 +138,9 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
 size_t fused_fp32_smem_bytes(int k);
 // False until the tensor-core kernel is compiled in.
 bool tc_available();
-size_t fused_tc_smem_bytes(bool split, int k);
+// Epilogue groups the tensor-core kernel runs with for k neighbours; each group
+// keeps its own row-side partial list per work unit.
+int tc_groups(int k);
+size_t fused_tc_smem_bytes(bool split, int k, int L);
 
 }  // namespace traknn

@@ -35,13 +35,22 @@ namespace {
 constexpr int BM = kTileRows;  // accumulator rows (TMEM lanes)
 constexpr int BN = 256;        // accumulator columns per tile
 constexpr int KC = 32;         // K elements per stage (64 B rows, 64-B swizzle)
-constexpr int kThreads = 192;
-constexpr int kEpiThreads = 128;
-constexpr int LDG = kHalo + 32 + 1;  // chunk buffer pitch (odd: conflict-free diagonals)
+constexpr int kEpiThreads = 128;  // one epilogue group: one thread per accumulator row
+// Threads of a CTA with NG epilogue groups (warp 0 producer, warp 1 MMA issuer).
+template <int NG>
+constexpr int threads_for() {
+  return 64 + kEpiThreads * NG;
+}
+// Pitch of the Gram chunk buffer: 32 columns plus the L-1 carried ones, made odd
+// so that the diagonal reads of 32 consecutive rows hit 32 different banks.
+__host__ __device__ constexpr int chunk_pitch(int L) {
+  return 32 + (L - 1) + (((L - 1) % 2 == 0) ? 1 : 0);
+}
 constexpr uint32_t kTileA = BM * KC * 2;  // bytes of one A operand tile
 constexpr uint32_t kTileB = BN * KC * 2;  // bytes of one B operand tile
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(BM, BN);
 constexpr int kMaxStages = 8;
+constexpr int kColCap = 24;  // column-side candidates buffered per column and chunk
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
 
 // Sorted (ascending distance) list of the K best candidates of one row, held in
@@ -62,6 +71,8 @@ struct RegList {
     }
   }
   __device__ __forceinline__ float threshold() const { return d[K - 1]; }
+  // Branch-free bubble: the list stays in registers (an early-exit form makes the
+  // compiler move it to local memory).
   __device__ __forceinline__ void insert(float x, int32_t xi) {
 #pragma unroll
     for (int p = 0; p < K; ++p) {
@@ -84,6 +95,13 @@ __device__ __forceinline__ bool key_before(float d, int32_t i, float ct, const S
   return i < cl.i[(cl.k - 1) * cl.stride + c];
 }
 
+// Shared memory of one epilogue group: Gram chunk with carried columns, W and row
+// bounds of a tile, column-side candidate buffers and counters, column lists.
+__host__ __device__ constexpr size_t group_bytes(int k, int L) {
+  return (size_t)BM * chunk_pitch(L) * 4 + 2 * BN * 4 + 32 * kColCap * 8 + 64 * 4 +
+         (size_t)32 * k * 8;
+}
+
 // Bits [lo, hi) of a 32-bit word (empty when hi <= lo).
 __device__ __forceinline__ uint32_t bit_range(int lo, int hi) {
   lo = max(lo, 0);
@@ -101,7 +119,6 @@ struct TcParams {
   uint32_t stage_bytes;
 };
 
-constexpr int kColCap = 16;  // column-side candidates buffered per column and chunk
 
 struct Ctl {
   volatile int* abort;
@@ -139,7 +156,10 @@ __device__ __forceinline__ bool unit_span(const Schedule& s, const TcWork& w, in
   us.jhi = wu.jhi;
   us.slot = wu.slot;
   if (us.jlo >= us.jhi) return false;
-  us.ntiles = (us.jhi - us.jlo + s.L - 1 + BN - 1) / BN;
+  // tiles overlap by L-1 Gram columns so that each one holds the whole window of
+  // its BN - (L-1) output columns
+  const int step = BN - (s.L - 1);
+  us.ntiles = (us.jhi - us.jlo + step - 1) / step;
   return true;
 }
 
@@ -156,8 +176,8 @@ __device__ __forceinline__ float kth_of(const RegList<K>& l, int k) {
 
 constexpr int kQueue = 4;  // depth of the per-CTA unit queue
 
-template <int K>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int K, int NG>
+__global__ void __launch_bounds__(threads_for<NG>(), 1)
     fused_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                     const __grid_constant__ CUtensorMap tmA_lo,
                     const __grid_constant__ CUtensorMap tmB_hi,
@@ -174,7 +194,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t ring = (raw + 1023u) & ~1023u;
   unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
-  float* Gbuf = reinterpret_cast<float*>(gptr);
+  // one region per epilogue group
+  const size_t gbytes = group_bytes(s.k, s.L);
+  const int LDG = chunk_pitch(s.L);
+  const int grp = warp >= 2 ? (warp - 2) >> 2 : 0;
+  unsigned char* gr = gptr + (size_t)grp * gbytes;
+  float* Gbuf = reinterpret_cast<float*>(gr);
   float* Wsh = Gbuf + BM * LDG;  // window sums of the tile's output columns
   float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
   float* Ed = Tsh + BN;          // [32][kColCap] column-side candidates: distance
@@ -182,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* ecount = Er + 32 * kColCap;  // [2][32] per-column counts, by chunk parity
   float* Cld = reinterpret_cast<float*>(ecount + 64);  // [k][32] column-side lists
   int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * s.k);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Cli + 32 * s.k);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + (size_t)NG * gbytes);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = full0 + 8u * NS;
   const uint32_t tfull0 = empty0 + 8u * NS;
@@ -211,10 +236,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::mbar_init(drain, 1);
     for (int i = 0; i < kQueue; ++i) {
       ptx::mbar_init(qfull0 + 8u * i, 1);
-      ptx::mbar_init(qempty0 + 8u * i, 2);  // the MMA thread and the epilogue leader
+      ptx::mbar_init(qempty0 + 8u * i, 1 + NG);  // the MMA thread and each group's leader
     }
     *abort_flag = 0;
-    for (int i = 0; i < 64; ++i) ecount[i] = 0;
+    for (int g = 0; g < NG; ++g) {
+      int* ec = reinterpret_cast<int*>(gptr + (size_t)g * gbytes +
+                                       ((size_t)BM * chunk_pitch(s.L) + 2 * BN + 32 * kColCap * 2) * 4);
+      for (int i = 0; i < 64; ++i) ec[i] = 0;
+    }
     ptx::fence_mbar_init();
     ptx::fence_proxy_async();
   }
@@ -255,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (u >= w.nunits) break;
         if (!unit_span(s, w, u, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
-          const int c0 = us.jlo + it * BN;
+          const int c0 = us.jlo + it * (BN - (s.L - 1));
           for (int kb = 0; kb < nkb; ++kb) {
             if (!wait_bounded(empty0 + 8u * stage, phase ^ 1u, ctl)) {
               ok = false;
@@ -293,9 +322,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int stage = 0, acc = 0, qs = 0;
-      uint32_t phase = 0, acc_phase = 0, qphase = 0;
+      int stage = 0, qs = 0, gt = 0;
+      uint32_t phase = 0, qphase = 0;
       bool ok = true, issued_any = false;
+      long long wait_tmem = 0, wait_full = 0;
+      const long long t_start = clock64();
       UnitSpan us;
       while (ok) {
         if (!wait_bounded(qfull0 + 8u * qs, qphase, ctl)) {
@@ -310,18 +341,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (u >= w.nunits) break;
         if (!unit_span(s, w, u, us)) continue;
-        for (int it = 0; ok && it < us.ntiles; ++it) {
-          if (!wait_bounded(tempty0 + 8u * acc, acc_phase ^ 1u, ctl)) {
+        for (int it = 0; ok && it < us.ntiles; ++it, ++gt) {
+          // tile gt uses accumulator gt & 1 for the (gt >> 1)-th time
+          const int acc = gt & 1;
+          const long long tw0 = w.stats ? clock64() : 0;
+          if (!wait_bounded(tempty0 + 8u * acc, ((gt >> 1) & 1) ^ 1u, ctl)) {
             ok = false;
             break;
           }
+          if (w.stats) wait_tmem += clock64() - tw0;
           ptx::tc_fence_after();
           const uint32_t d = tmem_base + (uint32_t)(acc * BN);
           for (int kb = 0; kb < nkb; ++kb) {
+            const long long tf0 = w.stats ? clock64() : 0;
             if (!wait_bounded(full0 + 8u * stage, phase, ctl)) {
               ok = false;
               break;
             }
+            if (w.stats) wait_full += clock64() - tf0;
             ptx::tc_fence_after();
             const uint32_t sb = ring + (uint32_t)stage * p.stage_bytes;
             const uint32_t a_hi = sb;
@@ -349,9 +386,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (!ok) break;
           ptx::mma_commit(tfull0 + 8u * acc);  // accumulator ready for the epilogue
-          acc ^= 1;
-          if (acc == 0) acc_phase ^= 1u;
         }
+      }
+      if (w.stats) {
+        atomicAdd(w.stats + kStatMmaWaitTmem, (unsigned long long)wait_tmem);
+        atomicAdd(w.stats + kStatMmaWaitFull, (unsigned long long)wait_full);
+        atomicAdd(w.stats + kStatMmaCycles, (unsigned long long)(clock64() - t_start));
       }
       if (!ok && issued_any) {
         // all MMAs of this thread must finish before TMEM is released
@@ -366,12 +406,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int l = q * 32 + lane;     // accumulator row owned by this thread
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     const int L = s.L;
-    const int et = threadIdx.x - 64;  // 0..127 within the epilogue group
-    const int cx = (warp - 2) * 8 + (lane & 7);  // column-side column of lanes 0..7
+    const int et = threadIdx.x - 64 - kEpiThreads * grp;  // 0..127 within the group
+    const int bar = 1 + grp;                               // the group's named barrier
+    const int cx = ((warp - 2) & 3) * 8 + (lane & 7);      // column-side column of lanes 0..7
     // the first chunk's emission counter was cleared at start-up; each chunk clears
     // the other counter for its successor
-    int acc = 0, qs = 0, gch = 0;
-    uint32_t acc_phase = 0, qphase = 0;
+    int qs = 0, gch = 0, gt = 0;
+    uint32_t qphase = 0;
     bool ok = true;
     UnitSpan us;
     RegList<K> list;
@@ -383,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     while (ok) {
       bool wok = wait_bounded(qfull0 + 8u * qs, qphase, ctl);
       const int u = wok ? qval[qs] : 0;
-      wok = ptx::named_bar_and(1, kEpiThreads, wok);  // everyone has read the slot
+      wok = ptx::named_bar_and(bar, kEpiThreads, wok);  // everyone has read the slot
       if (!wok) {
         ok = false;
         break;
@@ -400,15 +441,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float Wt = row_ok ? a.W[t] : 0.f;
       const int jsym = us.T0 + s.rows_out;  // column side from here on (sym)
       list.reset();
-      for (int it = 0; it < us.ntiles; ++it) {
-        wok = wait_bounded(tfull0 + 8u * acc, acc_phase, ctl);
-        wok = ptx::named_bar_and(1, kEpiThreads, wok);  // all four warps agree
+      for (int it = 0; it < us.ntiles; ++it, ++gt) {
+        if (NG > 1 && (gt % NG) != grp) continue;  // the other group's tile
+        const int acc = gt & 1;
+        wok = wait_bounded(tfull0 + 8u * acc, (gt >> 1) & 1, ctl);
+        wok = ptx::named_bar_and(bar, kEpiThreads, wok);  // all four warps agree
         if (!wok) {
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        const int c0 = us.jlo + it * BN;
+        const int c0 = us.jlo + it * (BN - (L - 1));
         // W and row bounds of this tile's output columns j = c0 - (L-1) + x (the
         // previous tile's readers passed its last barrier)
         for (int x = et; x < BN; x += kEpiThreads) {
@@ -418,37 +461,41 @@ __global__ void __launch_bounds__(kThreads, 1)
           Tsh[x] = in ? __uint_as_float(__ldcg(w.thr + j)) : 0.f;
         }
         const float thr_row = row_ok ? __uint_as_float(__ldcg(w.thr + t)) : 0.f;
+        // chunk ch+1 is read from TMEM while chunk ch is scanned
+        uint32_t vr[32];
+        ptx::tmem_ld32_async(tmem_base + lane_addr + (uint32_t)(acc * BN), vr);
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
-          float v[32];
-          ptx::tmem_ld32(tmem_base + lane_addr + (uint32_t)(acc * BN + ch * 32), v);
+          ptx::tmem_wait();
           float* grow = Gbuf + l * LDG;
-          if (it > 0 || ch > 0)
-            for (int c = 0; c < L - 1; ++c) grow[kHalo - (L - 1) + c] = grow[kHalo + 32 - (L - 1) + c];
+          if (ch > 0)
+            for (int c = 0; c < L - 1; ++c) grow[c] = grow[32 + c];
 #pragma unroll
-          for (int x = 0; x < 32; ++x) grow[kHalo + x] = v[x];
+          for (int x = 0; x < 32; ++x) grow[(L - 1) + x] = __uint_as_float(vr[x]);
+          if (ch + 1 < BN / 32)
+            ptx::tmem_ld32_async(tmem_base + lane_addr + (uint32_t)(acc * BN + (ch + 1) * 32), vr);
           if (ch == BN / 32 - 1) {
             // the accumulator has been read out: hand it back to the MMA warp
             ptx::tc_fence_before();
             ptx::mbar_arrive(tempty0 + 8u * acc);
           }
-          ptx::named_bar_sync(1, kEpiThreads);
+          ptx::named_bar_sync(bar, kEpiThreads);
           const int j0 = c0 + ch * 32 - (L - 1);
           const int eb = gch & 1;  // emission counters of this chunk
           // clear the next chunk's counters (their last readers passed this barrier)
           if (et < 32) ecount[(eb ^ 1) * 32 + et] = 0;
           // column side of this chunk: output columns j >= jsym inside the unit
           const uint32_t colrange = w.sym ? bit_range(max(jsym, us.jlo) - j0, us.jhi - j0) &
-                                                bit_range((it == 0 && ch == 0) ? L - 1 : 0, 32)
+                                                bit_range(ch == 0 ? L - 1 : 0, 32)
                                           : 0u;
           const float thr_col = Tsh[ch * 32 + cx];
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
-            // Gbuf[l+m][kHalo-(L-1)+x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
-            uint32_t valid = bit_range((it == 0 && ch == 0) ? L - 1 : 0, 32) &
+            // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
+            uint32_t valid = bit_range(ch == 0 ? L - 1 : 0, 32) &
                              bit_range(us.jlo - j0, us.jhi - j0);
             valid &= ~bit_range(t - s.e - j0, t + s.e + 1 - j0);  // exclusion zone
-            const float* g0 = Gbuf + l * LDG + kHalo - (L - 1);
+            const float* g0 = Gbuf + l * LDG;
             const float* wv = Wsh + ch * 32;
             const float* tv = Tsh + ch * 32;
             float c[32];
@@ -477,19 +524,23 @@ __global__ void __launch_bounds__(kThreads, 1)
               float cc = g0[x];
               for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + x];
               const float dv = fmaxf(fmaf(-2.0f, cc, Wt + wv[x]), 0.0f);
-              if ((cand & bit) && dv < list.threshold() && dv <= thr_row) list.insert(dv, j0 + x);
+              if ((cand & bit) && dv < list.threshold() && dv <= thr_row) {
+                list.insert(dv, j0 + x);
+                if (w.stats) atomicAdd(w.stats + kStatRowInserts, 1ull);
+              }
               if (ccand & bit) {
                 const int pos = atomicAdd(ecount + eb * 32 + x, 1);
                 if (pos < kColCap) {
                   Ed[x * kColCap + pos] = dv;
                   Er[x * kColCap + pos] = l;
                 }
+                if (w.stats) atomicAdd(w.stats + kStatColEmits, 1ull);
               }
               cand &= ~bit;
               ccand &= ~bit;
             }
           }
-          ptx::named_bar_sync(1, kEpiThreads);
+          ptx::named_bar_sync(bar, kEpiThreads);
           // every emission of this chunk happened before the barrier; a column that
           // overflowed its buffer is recomputed densely from the resident Gram chunk
           const int ne_lane = ecount[eb * 32 + lane];
@@ -513,10 +564,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                   }
                 }
               } else {
+                if (w.stats) atomicAdd(w.stats + kStatColDense, 1ull);
                 for (int r = 0; r < s.rows_out; ++r) {
                   const int tr = us.T0 + r;
                   if (tr >= s.M || (tr > j ? tr - j : j - tr) <= s.e) continue;
-                  const float* g0 = Gbuf + r * LDG + kHalo - (L - 1);
+                  const float* g0 = Gbuf + r * LDG;
                   float cc = g0[cx];
                   for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + cx];
                   const float dv = fmaxf(fmaf(-2.0f, cc, a.W[tr] + Wsh[ch * 32 + cx]), 0.0f);
@@ -527,6 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
               }
               n = min(n, s.k);
+              if (w.stats && n > 0) atomicAdd(w.stats + kStatColLists, 1ull);
               for (int pp = 0; pp < n; ++pp) {
                 w.col_d[li * s.k + pp] = cl.d[pp * 32 + cx];
                 w.col_i[li * s.k + pp] = cl.i[pp * 32 + cx];
@@ -537,11 +590,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           // the dense path read other rows' Gram values and Wsh: keep them in place
           // until it is done (uniform: every warp saw the same counters)
-          if (dense_any) ptx::named_bar_sync(1, kEpiThreads);
+          if (dense_any) ptx::named_bar_sync(bar, kEpiThreads);
+          if (w.stats && et == 0) atomicAdd(w.stats + kStatChunks, 1ull);
           ++gch;
         }
-        acc ^= 1;
-        if (acc == 0) acc_phase ^= 1u;
         if (row_ok) {
           const float kth = kth_of(list, s.k);
           if (kth < thr_row) atomicMin(w.thr + t, __float_as_uint(kth));
@@ -549,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (row_ok && w.write_lists) {
-        const size_t base = ((size_t)t * w.slots + us.slot) * s.k;
+        const size_t base = ((size_t)t * w.slots + us.slot * NG + grp) * s.k;
 #pragma unroll
         for (int pp = 0; pp < K; ++pp) {
           if (pp < s.k) {
@@ -600,14 +652,14 @@ bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t epilogue_bytes(int k) {
-  return (size_t)BM * LDG * 4 + 2 * BN * 4 + 32 * kColCap * 8 + 64 * 4 + (size_t)32 * k * 8 +
-         8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
+size_t epilogue_bytes(int k, int L, int ng) {
+  return (size_t)ng * group_bytes(k, L) + 8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue +
+         16;
 }
 
-int pick_stages(bool split, int k) {
+int pick_stages(bool split, int k, int L) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k);
+  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k, L, tc_groups(k));
   int ns = (int)(avail / stage);
   return ns < kMaxStages ? ns : kMaxStages;
 }
@@ -616,20 +668,29 @@ template <int K>
 cudaError_t launch_k(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUtensorMap& mBh,
                      const CUtensorMap& mBl, const TcParams& p, int num_ctas, size_t smem,
                      cudaStream_t st) {
-  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K>,
+  constexpr int NG = 1;
+  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K, NG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  fused_tc_kernel<K><<<num_ctas, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, p);
+  fused_tc_kernel<K, NG><<<num_ctas, threads_for<NG>(), smem, st>>>(mAh, mAl, mBh, mBl, p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+int tc_groups(int k) {
+  // One epilogue group: a second one fits the register file for k <= 20 but its
+  // shared memory costs a pipeline stage, which starves the tensor pipe more than
+  // the second group relieves the epilogue (measured).
+  (void)k;
+  return 1;
+}
+
 bool tc_available() { return encode_fn() != nullptr; }
 
-size_t fused_tc_smem_bytes(bool split, int k) {
+size_t fused_tc_smem_bytes(bool split, int k, int L) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  return 1024 + (size_t)pick_stages(split, k) * stage + epilogue_bytes(k);
+  return 1024 + (size_t)pick_stages(split, k, L) * stage + epilogue_bytes(k, L, tc_groups(k));
 }
 
 cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
@@ -650,9 +711,9 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Fu
   p.w = w;
   p.split = split ? 1 : 0;
   p.stage_bytes = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  p.nstages = pick_stages(split, a.sch.k);
+  p.nstages = pick_stages(split, a.sch.k, a.sch.L);
   if (p.nstages < 2) return cudaErrorInvalidValue;
-  const size_t smem = fused_tc_smem_bytes(split, a.sch.k);
+  const size_t smem = fused_tc_smem_bytes(split, a.sch.k, a.sch.L);
   const int k = a.sch.k;
   if (k <= 4) return launch_k<4>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
   if (k <= 8) return launch_k<8>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);

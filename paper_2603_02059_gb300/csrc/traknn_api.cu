@@ -41,6 +41,8 @@ struct traknn_ctx {
   // tensor-core work split
   int sym = 1;
   int unit_cols = 0;
+  int stats = 0;
+  unsigned long long* stats_dev = nullptr;
   struct {
     int M = -1, L = -1, k = -1, e = -1, sym = -1, cols = -1;
     int strips = 0, slots = 0, nunits = 0, nband = 0;
@@ -142,13 +144,15 @@ struct TcPlan {
   long long col_lists = 0;
 };
 
-TcPlan make_tc_plan(int M, int L, int sym, int cols_opt, int sm_count) {
+TcPlan make_tc_plan(int M, int L, int k, int sym, int cols_opt, int sm_count) {
   TcPlan p;
   const int R = kTileRows - (L - 1);
+  const int ng = tc_groups(k);  // row-side lists per unit and row
   p.strips = (M + R - 1) / R;
-  // a unit of n whole 256-column tiles covers 256 n - (L-1) output columns
-  const int cols = cols_opt > 0 ? cols_opt : 8 * 256 - (L - 1);
-  p.slots = (M + cols - 1) / cols;
+  // a tile yields 256 - (L-1) output columns; units are whole numbers of tiles
+  const int cols = cols_opt > 0 ? cols_opt : 16 * (256 - (L - 1));
+  const int chunks = (M + cols - 1) / cols;
+  p.slots = chunks * ng;
   const int group = std::max(1, std::min(p.strips, 19));
   (void)sm_count;
   p.col_off.resize(p.strips);
@@ -158,14 +162,14 @@ TcPlan make_tc_plan(int M, int L, int sym, int cols_opt, int sm_count) {
     p.col_off[s] = off;
     const long long first_col = (long long)(s + 1) * R;  // column side starts here
     if (sym && first_col < M) off += M - first_col;
-    p.slot_lo[s] = sym ? (s * R) / cols : 0;
+    p.slot_lo[s] = sym ? ((s * R) / cols) * ng : 0;
   }
   p.col_lists = off;
   const int ngroups = (p.strips + group - 1) / group;
   for (int gi = 0; gi < ngroups; ++gi) {
     const int g = sym ? ngroups - 1 - gi : gi;
     const int s_lo = g * group, s_hi = std::min(p.strips, s_lo + group);
-    for (int c = 0; c < p.slots; ++c)
+    for (int c = 0; c < chunks; ++c)
       for (int s = s_lo; s < s_hi; ++s) {
         const int T0 = s * R;
         int jlo = c * cols;
@@ -257,6 +261,7 @@ traknn_status traknn_destroy(traknn_handle h) {
   if (h->io) cudaFree(h->io);
   if (h->adj) cudaFree(h->adj);
   if (h->plan_dev) cudaFree(h->plan_dev);
+  if (h->stats_dev) cudaFree(h->stats_dev);
   if (h->err) cudaFree(h->err);
   for (int i = 0; i < traknn_ctx::kRing; ++i) {
     if (h->ev_start[i]) cudaEventDestroy(h->ev_start[i]);
@@ -294,6 +299,15 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
       if (v < 0 || v > (1 << 24)) return TRAKNN_ERR_INVALID_ARG;
       h->unit_cols = (int)v;
       return TRAKNN_OK;
+    case TRAKNN_OPT_STATS:
+      if (v && !h->stats_dev) {
+        if (cudaSetDevice(h->device) != cudaSuccess) return TRAKNN_ERR_CUDA;
+        if (cudaMalloc(&h->stats_dev, kStatCount * sizeof(unsigned long long)) != cudaSuccess)
+          return TRAKNN_ERR_ALLOC;
+        TRY_CUDA(cudaMemset(h->stats_dev, 0, kStatCount * sizeof(unsigned long long)));
+      }
+      h->stats = v ? 1 : 0;
+      return TRAKNN_OK;
     case TRAKNN_OPT_PROFILE:
       if (v && !h->ev_start[0]) {
         if (cudaSetDevice(h->device) != cudaSuccess) return TRAKNN_ERR_CUDA;
@@ -328,7 +342,7 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   auto& pl = h->plan;
   if (tc && (pl.M != M || pl.L != L || pl.k != k || pl.e != e || pl.sym != h->sym ||
              pl.cols != h->unit_cols)) {
-    TcPlan tp = make_tc_plan(M, L, h->sym, h->unit_cols, h->sm_count);
+    TcPlan tp = make_tc_plan(M, L, k, h->sym, h->unit_cols, h->sm_count);
     const size_t nb = tp.band.size();
     tp.units.insert(tp.units.end(), tp.band.begin(), tp.band.end());  // band units last
     const size_t ub = align_up(tp.units.size() * sizeof(WorkUnit), 256);
@@ -411,6 +425,7 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
     tw.col_i = reinterpret_cast<int32_t*>(ws + coli_off);
     tw.counter = reinterpret_cast<int*>(ws + cnt_off);
     tw.write_lists = 1;
+    tw.stats = h->stats ? h->stats_dev : nullptr;
   }
 
   TRY_CUDA(launch_col_mean(X, (int)N, (int)D, partial, mu, h->center != 0, s));
@@ -538,6 +553,20 @@ traknn_status traknn_profile_read(traknn_handle h, float* ms, int max_n, int* n_
   }
   *n_out = n;
   h->ev_head = h->ev_count = 0;
+  return TRAKNN_OK;
+}
+
+traknn_status traknn_stats_read(traknn_handle h, uint64_t* counters, int n) {
+  traknn_status st = check_handle(h);
+  if (st != TRAKNN_OK) return st;
+  if (!counters || n < 0) return TRAKNN_ERR_INVALID_ARG;
+  unsigned long long buf[kStatCount] = {};
+  if (h->stats_dev) {
+    TRY_CUDA(cudaDeviceSynchronize());
+    TRY_CUDA(cudaMemcpy(buf, h->stats_dev, sizeof(buf), cudaMemcpyDeviceToHost));
+    TRY_CUDA(cudaMemset(h->stats_dev, 0, sizeof(buf)));
+  }
+  for (int i = 0; i < n && i < kStatCount; ++i) counters[i] = buf[i];
   return TRAKNN_OK;
 }
 
