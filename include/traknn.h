@@ -77,7 +77,10 @@ typedef enum {
   TRAKNN_OPT_SYMMETRIC = 6,          /* tensor-core paths: 1 evaluates each unordered pair once
                                         (upper triangle, Sec. 3.3), 0 both triangles (default 1) */
   TRAKNN_OPT_UNIT_COLS = 7,          /* tensor-core paths: output columns per work unit, 0 = auto */
-  TRAKNN_OPT_STATS = 8               /* 1: count kernel events (read with traknn_stats_read) */
+  TRAKNN_OPT_STATS = 8,              /* 1: count kernel events (read with traknn_stats_read) */
+  TRAKNN_OPT_AUTOTUNE = 9            /* tensor-core paths: 1 times 8, 16 and 32 Gram tiles per work
+                                        unit on the first call of each shape and keeps the fastest
+                                        (ignored while TRAKNN_OPT_UNIT_COLS is set; default 0) */
 } traknn_option;
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */
@@ -127,6 +130,33 @@ traknn_status traknn_knn_scores_host(traknn_handle handle, const float* X_host, 
 traknn_status traknn_score_backward(traknn_handle handle, const float* X, int64_t N, int64_t D,
                                     int L, int k, const int32_t* nbr_idx,
                                     const float* grad_score, float* dX, void* stream);
+
+/* One series of a batched forward call: the arguments of traknn_knn_scores for
+ * one sequence of daily fields (device pointers). */
+typedef struct {
+  const float* X;     /* [N x D] float32, row-major */
+  int64_t N;          /* days */
+  int L;              /* trajectory length */
+  int k;              /* neighbours */
+  int exclusion;      /* temporal exclusion e */
+  int32_t* nbr_idx;   /* [M x k] out */
+  float* nbr_dist;    /* [M x k] out */
+  float* score;       /* [M] out */
+} traknn_series;
+
+/* Forward pass over B independent series that share the grid size D (each with
+ * its own N, L, k and exclusion; the method of Sec. 3.2 applied to each series
+ * separately, as when a study scores several regions, variables or ensemble
+ * members). Every series' outputs equal those of traknn_knn_scores on it alone.
+ * With a tensor-core precision up to 64 series run in one persistent launch
+ * sequence, which is captured as a CUDA graph on first use and replayed on later
+ * calls with the same shapes, pointers and options (the handle keeps one graph
+ * per such signature; a change of shape or a larger workspace drops them).
+ * With TRAKNN_PREC_FP32 the series run one after another. Each series is
+ * checked as traknn_check_problem would check it; the first failing series'
+ * status is returned before anything is enqueued. */
+traknn_status traknn_knn_scores_batched(traknn_handle handle, const traknn_series* series, int B,
+                                        int64_t D, void* stream);
 
 /* Forward pass for callers that cannot allocate device memory. There is no
  * counterpart in the paper: this is an interface addition of this library.

@@ -24,7 +24,15 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_AL
           8: "ERR_SCRATCH_LIMIT"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
-          "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7, "stats": 8}
+          "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7, "stats": 8,
+          "autotune": 9}
+
+
+class Series(ctypes.Structure):
+    """traknn_series of include/traknn.h (one series of a batched call)."""
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("L", ctypes.c_int),
+                ("k", ctypes.c_int), ("exclusion", ctypes.c_int), ("nbr_idx", ctypes.c_void_p),
+                ("nbr_dist", ctypes.c_void_p), ("score", ctypes.c_void_p)]
 
 
 class TrakNNError(RuntimeError):
@@ -60,6 +68,7 @@ def lib():
                 "traknn_launch_count": [P, ctypes.POINTER(I64)],
                 "traknn_knn_scores_static": [P, I64, I64, I, I, I, P, P, P, P],
                 "traknn_stats_read": [P, P, I],
+                "traknn_knn_scores_batched": [P, P, I, I64, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -115,7 +124,7 @@ class Handle:
         _check(lib().traknn_set_option(self._h, OPTION[name], int(value)), f"set_option({name})")
 
     def configure(self, precision=None, center=None, col_chunks=None, symmetric=None,
-                  unit_cols=None):
+                  unit_cols=None, autotune=None):
         if precision is not None:
             self.set_option("precision", PRECISION[precision])
         if center is not None:
@@ -126,6 +135,8 @@ class Handle:
             self.set_option("symmetric", int(symmetric))
         if unit_cols is not None:
             self.set_option("unit_cols", int(unit_cols))
+        if autotune is not None:
+            self.set_option("autotune", int(autotune))
 
     def profile_read(self, max_n: int = 256):
         """Durations (ms) of the fused Gram/top-k kernel of recent profiled calls."""
@@ -197,6 +208,46 @@ def knn_scores(X: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
                                  ctypes.c_void_p(s.cuda_stream))
     _check(rc, "traknn_knn_scores")
     return idx, dist, score
+
+
+def knn_scores_batched(series, *, precision: str = "split_bf16", center: bool = True,
+                       symmetric: bool = True, unit_cols: int = 0, autotune: bool = False,
+                       handle: Handle | None = None, outs=None):
+    """Forward pass of several series with the same grid size D in one call.
+    `series` is a list of (X, L, k, exclusion) with X a [N_b, D] float32 CUDA tensor
+    (exclusion None = L - 1). Returns a list of (idx, dist, score), one per series,
+    each equal to knn_scores on that series alone."""
+    if not series:
+        return []
+    Xs = [_as_input(X) for X, _, _, _ in series]
+    D = Xs[0].shape[1]
+    dev = Xs[0].device
+    for X in Xs:
+        if X.shape[1] != D or X.device != dev:
+            raise ValueError("all series must share D and the device")
+    h = handle or get_handle(dev.index)
+    h.configure(precision=precision, center=center, symmetric=symmetric, unit_cols=unit_cols,
+                autotune=autotune)
+    arr = (Series * len(series))()
+    results = []
+    for b, ((_, L, k, exclusion), X) in enumerate(zip(series, Xs)):
+        N = X.shape[0]
+        e = L - 1 if exclusion is None else int(exclusion)
+        M = max(N - L + 1, 0)
+        if outs is None:
+            idx = torch.empty((M, k), dtype=torch.int32, device=dev)
+            dist = torch.empty((M, k), dtype=torch.float32, device=dev)
+            score = torch.empty((M,), dtype=torch.float32, device=dev)
+        else:
+            idx, dist, score = outs[b]
+        arr[b] = Series(X.data_ptr(), N, L, k, e, idx.data_ptr(), dist.data_ptr(),
+                        score.data_ptr())
+        results.append((idx, dist, score))
+    s = torch.cuda.current_stream(dev)
+    rc = lib().traknn_knn_scores_batched(h._h, ctypes.cast(arr, ctypes.c_void_p), len(series),
+                                         D, ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_scores_batched")
+    return results
 
 
 def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,

@@ -67,34 +67,75 @@ struct FusedArgs {
   int debug_withhold;
 };
 
-// Work list of the tensor-core kernel. A unit is one row strip and one column
-// range; its Gram tiles are walked left to right with the diagonal carry.
-// With `sym` set only the upper triangle of the pair space is evaluated: strip s
-// covers columns j >= T0_s; inside its own block [T0_s, T0_s + rows_out) only the
-// rows collect candidates, beyond it every tile also gives each column j the
-// strip's rows as candidates (the column side), so every unordered pair is
-// evaluated once.
+// One series of a tensor-core call. A call processes one or more independent
+// series (same D, own N, L, k, exclusion); their operand copies are stacked in one
+// buffer and their trajectory rows in one index space.
+struct SeriesInfo {
+  int N, M, L, k;
+  int e;
+  int rows_out;         // output rows per strip: 128 - (L-1)
+  int row_base;         // first stacked operand row (day 0 of the series)
+  int out_base;         // first stacked trajectory row
+  int slots;            // row-side list slots per trajectory row
+  int strip_base;       // index of the series' strip 0 in col_off / slot_lo
+  long long part_base;  // first row-side list of the series
+  long long col_base;   // first column list of the series
+  const float* X;       // input [N][D]
+  int32_t* idx;         // outputs [M][k], [M][k], [M]
+  float* dist;
+  float* score;
+};
+
+// Series of one tensor-core launch, passed by value as a kernel parameter.
+constexpr int kMaxSeries = 64;
+struct SeriesTable {
+  int n;
+  int pad[3];
+  SeriesInfo s[kMaxSeries];
+};
+
+// Work list of the tensor-core kernel. A unit is one row strip of one series and
+// one column range; its Gram tiles are walked left to right. With `sym` set only
+// the upper triangle of each series' pair space is evaluated: strip s covers
+// columns j >= T0_s; inside its own block [T0_s, T0_s + rows_out) only the rows
+// collect candidates, beyond it every tile also gives each column j the strip's
+// rows as candidates (the column side), so every unordered pair is evaluated once.
 struct WorkUnit {
+  int series;
   int strip;  // row strip; output rows [strip*rows_out, (strip+1)*rows_out)
   int jlo;    // first output column
   int jhi;    // one past the last output column
   int slot;   // slot of the row-side partial lists written by this unit
+  int pad[3];
 };
 
 struct TcWork {
   const WorkUnit* units;
   int nunits;
-  int slots;                // row-side partial list slots per row
-  const int* slot_lo;       // [strips] first slot written for the strip's rows
+  int kstride;              // list stride (largest k of the call)
+  const long long* col_off; // [stacked strips] column-list offset within the series
+  const int* slot_lo;       // [stacked strips] first slot written for the strip's rows
   int sym;                  // 1: upper triangle + column side
-  const long long* col_off; // [strips] first column-list of strip s (sym only)
-  float* col_d;             // [lists][k] column-side candidate distances (sorted)
-  int32_t* col_i;           // [lists][k] column-side candidate rows
+  float* col_d;             // [lists][kstride] column-side candidate distances (sorted)
+  int32_t* col_i;           // [lists][kstride] column-side candidate rows
   int32_t* col_n;           // [lists] number of valid entries of each column list
-  unsigned int* thr;        // [M] bit patterns of an upper bound of each row's k-th distance
+  unsigned int* thr;        // [stacked rows] bit patterns of an upper bound of each row's k-th distance
   int* counter;             // next unit to hand out (zero before the launch)
   int write_lists;          // 0: only publish row bounds (band pre-pass)
   unsigned long long* stats;  // optional event counters (see kStat*), nullptr = off
+};
+
+struct TcArgs {
+  int Dp;              // padded row pitch of the stacked operand copies
+  int rows;            // stacked operand rows
+  int out_rows;        // stacked trajectory rows
+  int Lmax, kmax;      // largest L and k of the call (shared-memory sizing)
+  const float* W;      // [out_rows] window sums of day norms
+  float* part_d;       // [lists][kstride] row-side partial lists
+  int32_t* part_i;
+  int* err;
+  long long wait_limit_ns;
+  int debug_withhold;
 };
 
 // Event counters of the tensor-core kernel (diagnostics, TRAKNN_OPT_STATS).
@@ -121,12 +162,21 @@ cudaError_t launch_window(const double* norms, int M, int L, float* W, cudaStrea
 cudaError_t launch_fused_fp32(const float* Xc, const FusedArgs& a, int num_ctas,
                               cudaStream_t st);
 // Tensor-core path; `split` selects the 3-product split-BF16 form.
-cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
-                            const TcWork& w, int num_ctas, cudaStream_t st);
+cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const TcArgs& a,
+                            const TcWork& w, const SeriesTable& sr, int num_ctas, cudaStream_t st);
 // Final neighbour sets of the tensor-core path: candidates of every row's partial
-// lists (and column lists) that do not exceed its bound, then an exact top-k.
-cudaError_t launch_merge_tc(const FusedArgs& a, const TcWork& w, int32_t* idx, float* dist,
-                            float* score, cudaStream_t st);
+// lists (and column lists) that do not exceed its bound, then an exact top-k,
+// written to each series' output buffers.
+cudaError_t launch_merge_tc(const TcArgs& a, const TcWork& w, const SeriesTable& sr,
+                            cudaStream_t st);
+// Series-aware preparation for the tensor-core path (stacked operands).
+cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial, float* mu,
+                                   bool center, cudaStream_t st);
+cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int Dp,
+                                     bool even_aligned, const float* mu, void* hi, void* lo,
+                                     double* norms, cudaStream_t st);
+cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
+                                 float* W, cudaStream_t st);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
                          cudaStream_t st);
 // Adjoint of the summed weighted score (kernels_adjoint.cu); `ws` must hold
@@ -138,9 +188,7 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
 size_t fused_fp32_smem_bytes(int k);
 // False until the tensor-core kernel is compiled in.
 bool tc_available();
-// Epilogue groups the tensor-core kernel runs with for k neighbours; each group
-// keeps its own row-side partial list per work unit.
-int tc_groups(int k);
-size_t fused_tc_smem_bytes(bool split, int k, int L);
+
+size_t fused_tc_smem_bytes(bool split, int kmax, int Lmax);
 
 }  // namespace traknn

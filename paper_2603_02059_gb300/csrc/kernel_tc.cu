@@ -36,11 +36,8 @@ constexpr int BM = kTileRows;  // accumulator rows (TMEM lanes)
 constexpr int BN = 256;        // accumulator columns per tile
 constexpr int KC = 32;         // K elements per stage (64 B rows, 64-B swizzle)
 constexpr int kEpiThreads = 128;  // one epilogue group: one thread per accumulator row
-// Threads of a CTA with NG epilogue groups (warp 0 producer, warp 1 MMA issuer).
-template <int NG>
-constexpr int threads_for() {
-  return 64 + kEpiThreads * NG;
-}
+// Threads of a CTA: warp 0 producer, warp 1 MMA issuer, four epilogue warps.
+constexpr int kThreads = 64 + kEpiThreads;
 // Pitch of the Gram chunk buffer: 32 columns plus the L-1 carried ones, made odd
 // so that the diagonal reads of 32 consecutive rows hit 32 different banks.
 __host__ __device__ constexpr int chunk_pitch(int L) {
@@ -112,11 +109,12 @@ __device__ __forceinline__ uint32_t bit_range(int lo, int hi) {
 }
 
 struct TcParams {
-  FusedArgs a;
+  TcArgs a;
   TcWork w;
   int nstages;
   int split;
   uint32_t stage_bytes;
+  SeriesTable sr;
 };
 
 
@@ -143,22 +141,38 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, cons
   }
 }
 
+// A unit with its series' parameters.
 struct UnitSpan {
   int strip, T0, jlo, jhi, ntiles, slot;
+  int M, L, k, e, R;      // series: trajectories, length, neighbours, exclusion, rows per strip
+  int row_base, out_base, slots, strip_base;
+  long long part_base, col_base;
 };
 
-__device__ __forceinline__ bool unit_span(const Schedule& s, const TcWork& w, int u,
+__device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr, int u,
                                           UnitSpan& us) {
   const WorkUnit wu = w.units[u];
+  const SeriesInfo& si = sr[wu.series];
+  us.M = si.M;
+  us.L = si.L;
+  us.k = si.k;
+  us.e = si.e;
+  us.R = si.rows_out;
+  us.row_base = si.row_base;
+  us.out_base = si.out_base;
+  us.slots = si.slots;
+  us.strip_base = si.strip_base;
+  us.part_base = si.part_base;
+  us.col_base = si.col_base;
   us.strip = wu.strip;
-  us.T0 = wu.strip * s.rows_out;
+  us.T0 = wu.strip * us.R;
   us.jlo = wu.jlo;
   us.jhi = wu.jhi;
   us.slot = wu.slot;
   if (us.jlo >= us.jhi) return false;
   // tiles overlap by L-1 Gram columns so that each one holds the whole window of
   // its BN - (L-1) output columns
-  const int step = BN - (s.L - 1);
+  const int step = BN - (us.L - 1);
   us.ntiles = (us.jhi - us.jlo + step - 1) / step;
   return true;
 }
@@ -176,15 +190,15 @@ __device__ __forceinline__ float kth_of(const RegList<K>& l, int k) {
 
 constexpr int kQueue = 4;  // depth of the per-CTA unit queue
 
-template <int K, int NG>
-__global__ void __launch_bounds__(threads_for<NG>(), 1)
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1)
     fused_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                     const __grid_constant__ CUtensorMap tmA_lo,
                     const __grid_constant__ CUtensorMap tmB_hi,
-                    const __grid_constant__ CUtensorMap tmB_lo, const TcParams p) {
+                    const __grid_constant__ CUtensorMap tmB_lo,
+                    const __grid_constant__ TcParams p) {
   extern __shared__ unsigned char smem_raw[];
-  const FusedArgs& a = p.a;
-  const Schedule& s = a.sch;
+  const TcArgs& a = p.a;
   const TcWork& w = p.w;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -194,20 +208,17 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t ring = (raw + 1023u) & ~1023u;
   unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
-  // one region per epilogue group
-  const size_t gbytes = group_bytes(s.k, s.L);
-  const int LDG = chunk_pitch(s.L);
-  const int grp = warp >= 2 ? (warp - 2) >> 2 : 0;
-  unsigned char* gr = gptr + (size_t)grp * gbytes;
-  float* Gbuf = reinterpret_cast<float*>(gr);
-  float* Wsh = Gbuf + BM * LDG;  // window sums of the tile's output columns
+  // epilogue region, sized for the largest L and k of the call
+  const size_t gbytes = group_bytes(a.kmax, a.Lmax);
+  float* Gbuf = reinterpret_cast<float*>(gptr);
+  float* Wsh = Gbuf + BM * chunk_pitch(a.Lmax);  // window sums of the tile's output columns
   float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
   float* Ed = Tsh + BN;          // [32][kColCap] column-side candidates: distance
   int* Er = reinterpret_cast<int*>(Ed + 32 * kColCap);  // ... and accumulator row
   int* ecount = Er + 32 * kColCap;  // [2][32] per-column counts, by chunk parity
-  float* Cld = reinterpret_cast<float*>(ecount + 64);  // [k][32] column-side lists
-  int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * s.k);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + (size_t)NG * gbytes);
+  float* Cld = reinterpret_cast<float*>(ecount + 64);  // [kmax][32] column-side lists
+  int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * a.kmax);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + gbytes);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = full0 + 8u * NS;
   const uint32_t tfull0 = empty0 + 8u * NS;
@@ -236,14 +247,10 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
     ptx::mbar_init(drain, 1);
     for (int i = 0; i < kQueue; ++i) {
       ptx::mbar_init(qfull0 + 8u * i, 1);
-      ptx::mbar_init(qempty0 + 8u * i, 1 + NG);  // the MMA thread and each group's leader
+      ptx::mbar_init(qempty0 + 8u * i, 2);  // the MMA thread and the epilogue leader
     }
     *abort_flag = 0;
-    for (int g = 0; g < NG; ++g) {
-      int* ec = reinterpret_cast<int*>(gptr + (size_t)g * gbytes +
-                                       ((size_t)BM * chunk_pitch(s.L) + 2 * BN + 32 * kColCap * 2) * 4);
-      for (int i = 0; i < 64; ++i) ec[i] = 0;
-    }
+    for (int i = 0; i < 64; ++i) ecount[i] = 0;
     ptx::fence_mbar_init();
     ptx::fence_proxy_async();
   }
@@ -282,9 +289,10 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
           qphase ^= 1u;
         }
         if (u >= w.nunits) break;
-        if (!unit_span(s, w, u, us)) continue;
+        if (!unit_span(w, p.sr.s, u, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
-          const int c0 = us.jlo + it * (BN - (s.L - 1));
+          const int c0 = us.row_base + us.jlo + it * (BN - (us.L - 1));
+          const int a0 = us.row_base + us.T0;
           for (int kb = 0; kb < nkb; ++kb) {
             if (!wait_bounded(empty0 + 8u * stage, phase ^ 1u, ctl)) {
               ok = false;
@@ -296,9 +304,9 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
               const uint32_t fb = full0 + 8u * stage;
               const uint32_t sb = ring + (uint32_t)stage * p.stage_bytes;
               ptx::mbar_arrive_expect_tx(fb, p.stage_bytes);
-              ptx::tma_load_2d(sb, &tmA_hi, fb, kb * KC, us.T0);
+              ptx::tma_load_2d(sb, &tmA_hi, fb, kb * KC, a0);
               if (p.split) {
-                ptx::tma_load_2d(sb + kTileA, &tmA_lo, fb, kb * KC, us.T0);
+                ptx::tma_load_2d(sb + kTileA, &tmA_lo, fb, kb * KC, a0);
                 ptx::tma_load_2d(sb + 2 * kTileA, &tmB_hi, fb, kb * KC, c0);
                 ptx::tma_load_2d(sb + 2 * kTileA + kTileB, &tmB_lo, fb, kb * KC, c0);
               } else {
@@ -340,7 +348,7 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
           qphase ^= 1u;
         }
         if (u >= w.nunits) break;
-        if (!unit_span(s, w, u, us)) continue;
+        if (!unit_span(w, p.sr.s, u, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it, ++gt) {
           // tile gt uses accumulator gt & 1 for the (gt >> 1)-th time
           const int acc = gt & 1;
@@ -405,9 +413,8 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
     const int l = q * 32 + lane;     // accumulator row owned by this thread
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-    const int L = s.L;
-    const int et = threadIdx.x - 64 - kEpiThreads * grp;  // 0..127 within the group
-    const int bar = 1 + grp;                               // the group's named barrier
+    const int et = threadIdx.x - 64;  // 0..127 within the epilogue
+    const int bar = 1;                // the epilogue's named barrier
     const int cx = ((warp - 2) & 3) * 8 + (lane & 7);      // column-side column of lanes 0..7
     // the first chunk's emission counter was cleared at start-up; each chunk clears
     // the other counter for its successor
@@ -420,7 +427,6 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
     cl.d = Cld;
     cl.i = Cli;
     cl.stride = 32;
-    cl.k = s.k;
     while (ok) {
       bool wok = wait_bounded(qfull0 + 8u * qs, qphase, ctl);
       const int u = wok ? qval[qs] : 0;
@@ -435,14 +441,16 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
         qphase ^= 1u;
       }
       if (u >= w.nunits) break;
-      if (!unit_span(s, w, u, us)) continue;
+      if (!unit_span(w, p.sr.s, u, us)) continue;
+      const int L = us.L;
+      const int LDG = chunk_pitch(L);
+      cl.k = us.k;
       const int t = us.T0 + l;
-      const bool row_ok = l < s.rows_out && t < s.M;
-      const float Wt = row_ok ? a.W[t] : 0.f;
-      const int jsym = us.T0 + s.rows_out;  // column side from here on (sym)
+      const bool row_ok = l < us.R && t < us.M;
+      const float Wt = row_ok ? a.W[us.out_base + t] : 0.f;
+      const int jsym = us.T0 + us.R;  // column side from here on (sym)
       list.reset();
       for (int it = 0; it < us.ntiles; ++it, ++gt) {
-        if (NG > 1 && (gt % NG) != grp) continue;  // the other group's tile
         const int acc = gt & 1;
         wok = wait_bounded(tfull0 + 8u * acc, (gt >> 1) & 1, ctl);
         wok = ptx::named_bar_and(bar, kEpiThreads, wok);  // all four warps agree
@@ -456,11 +464,11 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
         // previous tile's readers passed its last barrier)
         for (int x = et; x < BN; x += kEpiThreads) {
           const int j = c0 - (L - 1) + x;
-          const bool in = j >= 0 && j < s.M;
-          Wsh[x] = in ? a.W[j] : 0.f;
-          Tsh[x] = in ? __uint_as_float(__ldcg(w.thr + j)) : 0.f;
+          const bool in = j >= 0 && j < us.M;
+          Wsh[x] = in ? a.W[us.out_base + j] : 0.f;
+          Tsh[x] = in ? __uint_as_float(__ldcg(w.thr + us.out_base + j)) : 0.f;
         }
-        const float thr_row = row_ok ? __uint_as_float(__ldcg(w.thr + t)) : 0.f;
+        const float thr_row = row_ok ? __uint_as_float(__ldcg(w.thr + us.out_base + t)) : 0.f;
         // chunk ch+1 is read from TMEM while chunk ch is scanned
         uint32_t vr[32];
         ptx::tmem_ld32_async(tmem_base + lane_addr + (uint32_t)(acc * BN), vr);
@@ -494,7 +502,7 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
             // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
             uint32_t valid = bit_range(ch == 0 ? L - 1 : 0, 32) &
                              bit_range(us.jlo - j0, us.jhi - j0);
-            valid &= ~bit_range(t - s.e - j0, t + s.e + 1 - j0);  // exclusion zone
+            valid &= ~bit_range(t - us.e - j0, t + us.e + 1 - j0);  // exclusion zone
             const float* g0 = Gbuf + l * LDG;
             const float* wv = Wsh + ch * 32;
             const float* tv = Tsh + ch * 32;
@@ -548,7 +556,7 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
           if (colrange && lane < 8 && ((colrange >> cx) & 1u)) {
             // the column's candidates among the strip's rows, kept in (distance, row) order
             const int j = j0 + cx;
-            const long long li = w.col_off[us.strip] + (j - jsym);
+            const long long li = us.col_base + w.col_off[us.strip_base + us.strip] + (j - jsym);
             const int ne = ecount[eb * 32 + cx];
             int n = 0;
             float ct = CUDART_INF_F;
@@ -565,28 +573,29 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
                 }
               } else {
                 if (w.stats) atomicAdd(w.stats + kStatColDense, 1ull);
-                for (int r = 0; r < s.rows_out; ++r) {
+                for (int r = 0; r < us.R; ++r) {
                   const int tr = us.T0 + r;
-                  if (tr >= s.M || (tr > j ? tr - j : j - tr) <= s.e) continue;
+                  if (tr >= us.M || (tr > j ? tr - j : j - tr) <= us.e) continue;
                   const float* g0 = Gbuf + r * LDG;
                   float cc = g0[cx];
                   for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + cx];
-                  const float dv = fmaxf(fmaf(-2.0f, cc, a.W[tr] + Wsh[ch * 32 + cx]), 0.0f);
+                  const float dv =
+                      fmaxf(fmaf(-2.0f, cc, a.W[us.out_base + tr] + Wsh[ch * 32 + cx]), 0.0f);
                   if (dv <= thr_col && dv < ct) {
                     ct = cl.insert(cx, dv, tr);
                     ++n;
                   }
                 }
               }
-              n = min(n, s.k);
+              n = min(n, us.k);
               if (w.stats && n > 0) atomicAdd(w.stats + kStatColLists, 1ull);
               for (int pp = 0; pp < n; ++pp) {
-                w.col_d[li * s.k + pp] = cl.d[pp * 32 + cx];
-                w.col_i[li * s.k + pp] = cl.i[pp * 32 + cx];
+                w.col_d[li * w.kstride + pp] = cl.d[pp * 32 + cx];
+                w.col_i[li * w.kstride + pp] = cl.i[pp * 32 + cx];
               }
             }
             w.col_n[li] = n;
-            if (n == s.k) atomicMin(w.thr + j, __float_as_uint(ct));
+            if (n == us.k) atomicMin(w.thr + us.out_base + j, __float_as_uint(ct));
           }
           // the dense path read other rows' Gram values and Wsh: keep them in place
           // until it is done (uniform: every warp saw the same counters)
@@ -595,16 +604,16 @@ __global__ void __launch_bounds__(threads_for<NG>(), 1)
           ++gch;
         }
         if (row_ok) {
-          const float kth = kth_of(list, s.k);
-          if (kth < thr_row) atomicMin(w.thr + t, __float_as_uint(kth));
+          const float kth = kth_of(list, us.k);
+          if (kth < thr_row) atomicMin(w.thr + us.out_base + t, __float_as_uint(kth));
         }
       }
       if (!ok) break;
       if (row_ok && w.write_lists) {
-        const size_t base = ((size_t)t * w.slots + us.slot * NG + grp) * s.k;
+        const size_t base = (size_t)(us.part_base + (long long)t * us.slots + us.slot) * w.kstride;
 #pragma unroll
         for (int pp = 0; pp < K; ++pp) {
-          if (pp < s.k) {
+          if (pp < us.k) {
             a.part_d[base + pp] = list.d[pp];
             a.part_i[base + pp] = list.i[pp];
           }
@@ -652,14 +661,13 @@ bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t epilogue_bytes(int k, int L, int ng) {
-  return (size_t)ng * group_bytes(k, L) + 8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue +
-         16;
+size_t epilogue_bytes(int k, int L) {
+  return group_bytes(k, L) + 8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
 }
 
 int pick_stages(bool split, int k, int L) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k, L, tc_groups(k));
+  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k, L);
   int ns = (int)(avail / stage);
   return ns < kMaxStages ? ns : kMaxStages;
 }
@@ -668,53 +676,45 @@ template <int K>
 cudaError_t launch_k(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUtensorMap& mBh,
                      const CUtensorMap& mBl, const TcParams& p, int num_ctas, size_t smem,
                      cudaStream_t st) {
-  constexpr int NG = 1;
-  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K, NG>,
+  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  fused_tc_kernel<K, NG><<<num_ctas, threads_for<NG>(), smem, st>>>(mAh, mAl, mBh, mBl, p);
+  fused_tc_kernel<K><<<num_ctas, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc_groups(int k) {
-  // One epilogue group: a second one fits the register file for k <= 20 but its
-  // shared memory costs a pipeline stage, which starves the tensor pipe more than
-  // the second group relieves the epilogue (measured).
-  (void)k;
-  return 1;
-}
-
 bool tc_available() { return encode_fn() != nullptr; }
 
-size_t fused_tc_smem_bytes(bool split, int k, int L) {
+size_t fused_tc_smem_bytes(bool split, int kmax, int Lmax) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  return 1024 + (size_t)pick_stages(split, k, L) * stage + epilogue_bytes(k, L, tc_groups(k));
+  return 1024 + (size_t)pick_stages(split, kmax, Lmax) * stage + epilogue_bytes(kmax, Lmax);
 }
 
-cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const FusedArgs& a,
-                            const TcWork& w, int num_ctas, cudaStream_t st) {
+cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const TcArgs& a,
+                            const TcWork& w, const SeriesTable& sr, int num_ctas, cudaStream_t st) {
   if (a.Dp % KC != 0) return cudaErrorInvalidValue;
   CUtensorMap mAh, mAl, mBh, mBl;
-  if (!make_map(&mAh, hi, a.N, a.Dp, BM) || !make_map(&mBh, hi, a.N, a.Dp, BN))
+  if (!make_map(&mAh, hi, a.rows, a.Dp, BM) || !make_map(&mBh, hi, a.rows, a.Dp, BN))
     return cudaErrorNotSupported;
   if (split) {
-    if (!make_map(&mAl, lo, a.N, a.Dp, BM) || !make_map(&mBl, lo, a.N, a.Dp, BN))
+    if (!make_map(&mAl, lo, a.rows, a.Dp, BM) || !make_map(&mBl, lo, a.rows, a.Dp, BN))
       return cudaErrorNotSupported;
   } else {
     mAl = mAh;
     mBl = mBh;
   }
-  TcParams p;
+  thread_local TcParams p;  // large (series table): kept off the stack
   p.a = a;
   p.w = w;
+  p.sr = sr;
   p.split = split ? 1 : 0;
   p.stage_bytes = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  p.nstages = pick_stages(split, a.sch.k, a.sch.L);
+  p.nstages = pick_stages(split, a.kmax, a.Lmax);
   if (p.nstages < 2) return cudaErrorInvalidValue;
-  const size_t smem = fused_tc_smem_bytes(split, a.sch.k, a.sch.L);
-  const int k = a.sch.k;
+  const size_t smem = fused_tc_smem_bytes(split, a.kmax, a.Lmax);
+  const int k = a.kmax;
   if (k <= 4) return launch_k<4>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
   if (k <= 8) return launch_k<8>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
   if (k <= 10) return launch_k<10>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);

@@ -139,6 +139,135 @@ __global__ void __launch_bounds__(256)
   if (lane == 0) norms[a] = acc;
 }
 
+// Index of the series whose [base, base + count) range of stacked rows holds r.
+__device__ __forceinline__ int find_series(const SeriesInfo* sr, int ns, int r, bool traj) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int base = traj ? sr[mid].out_base : sr[mid].row_base;
+    if (base <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Column sums of every series over fixed row slices (grid.z = series).
+__global__ void col_partial_series_kernel(const __grid_constant__ SeriesTable st, int D,
+                                          float* partial) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= D) return;
+  const SeriesInfo& si = st.s[blockIdx.z];
+  const int per = (si.N + kMeanSlices - 1) / kMeanSlices;
+  const int r0 = blockIdx.y * per, r1 = min(si.N, r0 + per);
+  float acc = 0.f;
+  for (int a = r0; a < r1; ++a) acc += si.X[(size_t)a * D + p];
+  partial[((size_t)blockIdx.z * kMeanSlices + blockIdx.y) * D + p] = acc;
+}
+
+__global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
+                                        const float* partial, int D, float* mu, int center) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= D) return;
+  const int b = blockIdx.y;
+  if (!center) {
+    mu[(size_t)b * D + p] = 0.f;
+    return;
+  }
+  float acc = 0.f;
+  for (int s = 0; s < kMeanSlices; ++s) acc += partial[((size_t)b * kMeanSlices + s) * D + p];
+  mu[(size_t)b * D + p] = acc / (float)st.s[b].N;
+}
+
+// One warp per stacked day: x - mu(series) = hi + lo (two BF16 copies, pitch Dp) and
+// the FP64 norm of the centred row; FP32 squares summed 8 at a time before joining
+// the FP64 accumulator. VEC = 2 reads pairs (even D, 8-byte aligned rows).
+template <int VEC>
+__global__ void __launch_bounds__(256)
+    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int Dp,
+                             const float* __restrict__ mu, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo, double* __restrict__ norms) {
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const int b = find_series(st.s, st.n, r, false);
+  const SeriesInfo& si = st.s[b];
+  const int a = r - si.row_base;
+  const float* x = si.X + (size_t)a * D;
+  const float* m = mu + (size_t)b * D;
+  __nv_bfloat16* h = hi + (size_t)r * Dp;
+  __nv_bfloat16* lw = lo + (size_t)r * Dp;
+  double acc = 0.0;
+  float part = 0.f;
+  int cnt = 0;
+  if (a >= si.N) {  // padding row between series: zeros
+    for (int q = lane; q < Dp; q += 32) {
+      h[q] = __float2bfloat16_rn(0.f);
+      lw[q] = __float2bfloat16_rn(0.f);
+    }
+    if (lane == 0) norms[r] = 0.0;
+    return;
+  }
+  if (VEC == 2) {
+    const float2* x2 = reinterpret_cast<const float2*>(x);
+    const float2* m2 = reinterpret_cast<const float2*>(m);
+    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(h);
+    __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(lw);
+    for (int q = lane; q < Dp / 2; q += 32) {
+      float2 v = make_float2(0.f, 0.f);
+      if (q < D / 2) {
+        const float2 xv = x2[q];
+        const float2 mv = m2[q];
+        v = make_float2(xv.x - mv.x, xv.y - mv.y);
+      }
+      const __nv_bfloat162 hv = __floats2bfloat162_rn(v.x, v.y);
+      const float2 hf = __bfloat1622float2(hv);
+      h2[q] = hv;
+      l2[q] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+      part = fmaf(v.x, v.x, part);
+      part = fmaf(v.y, v.y, part);
+      if (++cnt == 4) {
+        acc += (double)part;
+        part = 0.f;
+        cnt = 0;
+      }
+    }
+  } else {
+    for (int q = lane; q < Dp; q += 32) {
+      const float v = q < D ? x[q] - m[q] : 0.f;
+      const __nv_bfloat16 hv = __float2bfloat16_rn(v);
+      h[q] = hv;
+      lw[q] = __float2bfloat16_rn(v - __bfloat162float(hv));
+      part = fmaf(v, v, part);
+      if (++cnt == 8) {
+        acc += (double)part;
+        part = 0.f;
+        cnt = 0;
+      }
+    }
+  }
+  acc += (double)part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norms[r] = acc;
+}
+
+// W of every stacked trajectory row: an explicit L-term FP64 sum of its series' norms.
+__global__ void window_series_kernel(const __grid_constant__ SeriesTable st, int out_rows,
+                                     const double* __restrict__ norms, float* W) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= out_rows) return;
+  const int b = find_series(st.s, st.n, r, true);
+  const SeriesInfo& si = st.s[b];
+  const int t = r - si.out_base;
+  if (t >= si.M) {
+    W[r] = 0.f;
+    return;
+  }
+  double s = 0.0;
+  for (int m = 0; m < si.L; ++m) s += norms[si.row_base + t + m];
+  W[r] = (float)s;
+}
+
 // W_t = sum_{m<L} n_{t+m}: an explicit L-term FP64 sum per trajectory.
 __global__ void window_kernel(const double* __restrict__ norms, int M, int L, float* W) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,18 +339,25 @@ __device__ __forceinline__ bool key_less(float d1, int i1, float d2, int i2) {
 // set overflows the buffer, the rounds scan the lists directly.
 __global__ void __launch_bounds__(32 * kMergeWarps)
     merge_tc_kernel(const float* __restrict__ part_d, const int32_t* __restrict__ part_i,
-                    Schedule s, TcWork w, int32_t* __restrict__ idx, float* __restrict__ dist,
-                    float* __restrict__ score) {
+                    int out_rows, TcWork w, const __grid_constant__ SeriesTable st) {
   __shared__ float bd[kMergeWarps][kMergeCap];
   __shared__ int bi[kMergeWarps][kMergeCap];
   __shared__ int bn[kMergeWarps];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * kMergeWarps + wid;
-  if (t >= s.M) return;
-  const int k = s.k;
-  const int strip = t / s.rows_out;
-  float thr = __uint_as_float(w.thr[t]);
-  const int c_lo = w.slot_lo[strip];
+  const int r = blockIdx.x * kMergeWarps + wid;
+  if (r >= out_rows) return;
+  const int sidx = find_series(st.s, st.n, r, true);
+  const SeriesInfo& si = st.s[sidx];
+  const int t = r - si.out_base;
+  if (t >= si.M) return;
+  const int k = si.k, ks = w.kstride;
+  const int strip = t / si.rows_out;
+  float thr = __uint_as_float(w.thr[r]);
+  const int c_lo = w.slot_lo[si.strip_base + strip];
+  const long long plist = si.part_base + (long long)t * si.slots;  // first row-side list
+  auto collist = [&](int s2) {
+    return si.col_base + w.col_off[si.strip_base + s2] + (t - (s2 + 1) * si.rows_out);
+  };
   auto push = [&](float d, int i) {
     const int pos = atomicAdd(&bn[wid], 1);
     if (pos < kMergeCap) {
@@ -229,11 +365,10 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       bi[wid][pos] = i;
     }
   };
-  // k rounds of a warp arg-min over the buffer (strictly after the previous pick)
-  auto select = [&](int n, float* outd, int* outi) {
+  auto select = [&](int n) {
     float last_d = -CUDART_INF_F;
     int last_i = -1;
-    for (int r = 0; r < k; ++r) {
+    for (int rr = 0; rr < k; ++rr) {
       float best_d = CUDART_INF_F;
       int best_i = INT_MAX;
       for (int q = lane; q < n; q += 32) {
@@ -255,10 +390,6 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
       last_d = best_d;
       last_i = best_i;
-      if (outd) {
-        outd[r] = best_d;
-        outi[r] = best_i;
-      }
     }
     return last_d;
   };
@@ -266,8 +397,8 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
   for (int pass = 0; pass < 64; ++pass) {
     if (lane == 0) bn[wid] = 0;
     __syncwarp();
-    for (int c = c_lo + lane; c < w.slots; c += 32) {
-      const size_t b = ((size_t)t * w.slots + c) * k;
+    for (int c = c_lo + lane; c < si.slots; c += 32) {
+      const size_t b = (size_t)(plist + c) * ks;
       for (int p = 0; p < k; ++p) {
         const int ii = part_i[b + p];
         const float d = part_d[b + p];
@@ -277,12 +408,12 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     }
     if (w.sym) {
       for (int s2 = lane; s2 < strip; s2 += 32) {
-        const long long li = w.col_off[s2] + (t - (s2 + 1) * s.rows_out);
+        const long long li = collist(s2);
         const int nn = w.col_n[li];
         for (int p = 0; p < nn; ++p) {
-          const float d = w.col_d[li * k + p];
+          const float d = w.col_d[li * ks + p];
           if (d > thr) break;
-          push(d, w.col_i[li * k + p]);
+          push(d, w.col_i[li * ks + p]);
         }
       }
     }
@@ -292,7 +423,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     if (n <= kMergeCap) break;
     // overflow: the k-th smallest of the buffered (valid, distinct) candidates is a
     // tighter bound; gather again under it
-    thr = select(kMergeCap, nullptr, nullptr);
+    thr = select(kMergeCap);
   }
   // final selection, written in (distance, index) order; if ties at the bound keep
   // the candidate set larger than the buffer, scan the lists directly each round
@@ -300,7 +431,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
   float last_d = -CUDART_INF_F;
   int last_i = -1;
   double sum = 0.0;
-  for (int r = 0; r < k; ++r) {
+  for (int rr = 0; rr < k; ++rr) {
     float best_d = CUDART_INF_F;
     int best_i = INT_MAX;
     auto consider = [&](float d, int ii) {
@@ -312,8 +443,8 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     if (!direct) {
       for (int q = lane; q < n; q += 32) consider(bd[wid][q], bi[wid][q]);
     } else {
-      for (int c = c_lo + lane; c < w.slots; c += 32) {
-        const size_t b = ((size_t)t * w.slots + c) * k;
+      for (int c = c_lo + lane; c < si.slots; c += 32) {
+        const size_t b = (size_t)(plist + c) * ks;
         for (int p = 0; p < k; ++p) {
           const int ii = part_i[b + p];
           if (ii < 0 || part_d[b + p] > thr) break;
@@ -322,11 +453,11 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
       if (w.sym) {
         for (int s2 = lane; s2 < strip; s2 += 32) {
-          const long long li = w.col_off[s2] + (t - (s2 + 1) * s.rows_out);
+          const long long li = collist(s2);
           const int nn = w.col_n[li];
           for (int p = 0; p < nn; ++p) {
-            if (w.col_d[li * k + p] > thr) break;
-            consider(w.col_d[li * k + p], w.col_i[li * k + p]);
+            if (w.col_d[li * ks + p] > thr) break;
+            consider(w.col_d[li * ks + p], w.col_i[li * ks + p]);
           }
         }
       }
@@ -343,21 +474,52 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     last_d = best_d;
     last_i = best_i;
     if (lane == 0) {
-      idx[(size_t)t * k + r] = best_i == INT_MAX ? -1 : best_i;
-      dist[(size_t)t * k + r] = best_d;
+      si.idx[(size_t)t * k + rr] = best_i == INT_MAX ? -1 : best_i;
+      si.dist[(size_t)t * k + rr] = best_d;
       sum += (double)best_d;
     }
   }
-  if (lane == 0) score[t] = (float)(sum / (double)k);
+  if (lane == 0) si.score[t] = (float)(sum / (double)k);
 }
 
 }  // namespace
 
-cudaError_t launch_merge_tc(const FusedArgs& a, const TcWork& w, int32_t* idx, float* dist,
-                            float* score, cudaStream_t st) {
-  const int blocks = (a.sch.M + kMergeWarps - 1) / kMergeWarps;
-  merge_tc_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(a.part_d, a.part_i, a.sch, w, idx, dist,
-                                                       score);
+cudaError_t launch_merge_tc(const TcArgs& a, const TcWork& w, const SeriesTable& sr,
+                            cudaStream_t st) {
+  const int blocks = (a.out_rows + kMergeWarps - 1) / kMergeWarps;
+  merge_tc_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(a.part_d, a.part_i, a.out_rows, w, sr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial, float* mu,
+                                   bool center, cudaStream_t st) {
+  if (center) {
+    dim3 grid((D + 255) / 256, kMeanSlices, sr.n);
+    col_partial_series_kernel<<<grid, 256, 0, st>>>(sr, D, partial);
+  }
+  dim3 g2((D + 255) / 256, sr.n);
+  col_final_series_kernel<<<g2, 256, 0, st>>>(sr, partial, D, mu, center ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int Dp,
+                                     bool even_aligned, const float* mu, void* hi, void* lo,
+                                     double* norms, cudaStream_t st) {
+  const int blocks = (rows + 7) / 8;
+  if (even_aligned)
+    prep_split_series_kernel<2><<<blocks, 256, 0, st>>>(sr, rows, D, Dp, mu,
+                                                        static_cast<__nv_bfloat16*>(hi),
+                                                        static_cast<__nv_bfloat16*>(lo), norms);
+  else
+    prep_split_series_kernel<1><<<blocks, 256, 0, st>>>(sr, rows, D, Dp, mu,
+                                                        static_cast<__nv_bfloat16*>(hi),
+                                                        static_cast<__nv_bfloat16*>(lo), norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
+                                 float* W, cudaStream_t st) {
+  window_series_kernel<<<(out_rows + 255) / 256, 256, 0, st>>>(sr, out_rows, norms, W);
   return cudaGetLastError();
 }
 

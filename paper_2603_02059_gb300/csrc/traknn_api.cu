@@ -1,6 +1,7 @@
 // traknn_api.cu -- the C ABI declared in include/traknn.h: argument checks,
-// workspace management and the launch sequence of the forward and backward
-// passes. All arithmetic runs in the kernels of the other translation units.
+// workspace management, work planning and the launch sequences of the forward
+// (single series and batched) and backward passes. All arithmetic runs in the
+// kernels of the other translation units.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +16,37 @@
 
 using namespace traknn;
 
+namespace {
+
+// One series of a tensor-core call as the caller describes it.
+struct HostSeries {
+  const float* X;
+  int64_t N;
+  int L, k, e;
+  int32_t* idx;
+  float* dist;
+  float* score;
+};
+
+// Work list and layout of one tensor-core call (all series of a batch).
+struct TcPlan {
+  std::vector<int64_t> key;     // D, options and per-series shapes the plan was built for
+  SeriesTable table;            // output and input pointers filled per call
+  std::vector<WorkUnit> units;  // main units, then the band units
+  int nunits = 0, nband = 0;
+  std::vector<long long> col_off;
+  std::vector<int> slot_lo;
+  int rows = 0, out_rows = 0, kmax = 0, Lmax = 0;
+  long long part_lists = 0, col_lists = 0;
+};
+
+struct GraphEntry {
+  std::vector<int64_t> key;  // plan key, pointers and options
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
 struct traknn_ctx {
   int device = 0;
   int sm_count = 0;
@@ -24,8 +56,10 @@ struct traknn_ctx {
   int wait_limit_ms = 2000;
   int debug_withhold = 0;
   // library-owned buffers, grown on demand
-  void* ws = nullptr;
+  void* ws = nullptr;  // FP32 path
   size_t ws_bytes = 0;
+  void* tcws = nullptr;  // tensor-core path
+  size_t tcws_bytes = 0;
   void* io = nullptr;  // device staging for the host-buffer entry point
   size_t io_bytes = 0;
   void* adj = nullptr;  // reverse neighbour index of the adjoint
@@ -41,22 +75,20 @@ struct traknn_ctx {
   // tensor-core work split
   int sym = 1;
   int unit_cols = 0;
+  int autotune = 0;
   int stats = 0;
   unsigned long long* stats_dev = nullptr;
-  struct {
-    int M = -1, L = -1, k = -1, e = -1, sym = -1, cols = -1;
-    int strips = 0, slots = 0, nunits = 0, nband = 0;
-    long long col_lists = 0;
-    size_t bytes = 0;
-  } plan;
-  void* plan_dev = nullptr;  // units, col_off, slot_lo
+  TcPlan plan;
+  void* plan_dev = nullptr;  // units, col_off, slot_lo of `plan`
   size_t plan_dev_bytes = 0;
+  std::vector<std::pair<std::vector<int64_t>, int>> tuned;  // shape key -> tiles per unit
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
 
 #define TRY_CUDA(expr)                              \
   do {                                              \
@@ -64,8 +96,22 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
     if (e_ != cudaSuccess) return TRAKNN_ERR_CUDA;  \
   } while (0)
 
-traknn_status ensure_buffer(void** buf, size_t* have, size_t need) {
+#define TRY_ST(expr)                  \
+  do {                                \
+    traknn_status s_ = (expr);        \
+    if (s_ != TRAKNN_OK) return s_;   \
+  } while (0)
+
+void drop_graphs(traknn_ctx* h) {
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
+// Grow a library buffer. Captured graphs refer to the old buffers, so they go too.
+traknn_status ensure_buffer(traknn_ctx* h, void** buf, size_t* have, size_t need) {
   if (*have >= need) return TRAKNN_OK;
+  drop_graphs(h);
   if (*buf) {
     cudaDeviceSynchronize();
     cudaFree(*buf);
@@ -82,7 +128,7 @@ traknn_status ensure_buffer(void** buf, size_t* have, size_t need) {
   return TRAKNN_OK;
 }
 
-// Work split of the M x M pair space (see Schedule in internal.h).
+// Work split of the M x M pair space of the FP32 path (see Schedule in internal.h).
 Schedule make_schedule(int M, int L, int k, int e, int sm_count, int chunks_opt) {
   Schedule s;
   s.M = M;
@@ -121,79 +167,373 @@ Layout make_layout(int64_t N, int64_t D, const Schedule& s) {
   l.mu = take((size_t)D * sizeof(float));
   l.norms = take((size_t)N * sizeof(double));
   l.W = take((size_t)s.M * sizeof(float));
-  // FP32 centred copy, or hi and lo BF16 copies: 4 bytes per element either way
-  l.ops = take((size_t)N * l.Dp * 4);
+  l.ops = take((size_t)N * l.Dp * 4);  // centred FP32 copy
   l.pd = take((size_t)s.M * s.chunks * s.k * sizeof(float));
   l.pi = take((size_t)s.M * s.chunks * s.k * sizeof(int32_t));
   l.total = off;
   return l;
 }
 
-// Tensor-core work list. Units (strip, column range) are ordered in groups of
-// strips that run side by side (sharing A and B tiles in L2); with the symmetric
-// split the groups go from the last strip upwards, so the rows whose own lists
-// bound the column side of a strip have mostly been processed before it.
-static_assert(sizeof(WorkUnit) == 16, "work unit layout");
+static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 
-struct TcPlan {
-  std::vector<WorkUnit> units;
-  std::vector<WorkUnit> band;  // threshold pre-pass: one unit around each strip's diagonal
-  std::vector<long long> col_off;
-  std::vector<int> slot_lo;
-  int strips = 0, slots = 0;
-  long long col_lists = 0;
-};
-
-TcPlan make_tc_plan(int M, int L, int k, int sym, int cols_opt, int sm_count) {
-  TcPlan p;
-  const int R = kTileRows - (L - 1);
-  const int ng = tc_groups(k);  // row-side lists per unit and row
-  p.strips = (M + R - 1) / R;
-  // a tile yields 256 - (L-1) output columns; units are whole numbers of tiles
-  const int cols = cols_opt > 0 ? cols_opt : 16 * (256 - (L - 1));
-  const int chunks = (M + cols - 1) / cols;
-  p.slots = chunks * ng;
-  const int group = std::max(1, std::min(p.strips, 19));
-  (void)sm_count;
-  p.col_off.resize(p.strips);
-  p.slot_lo.resize(p.strips);
-  long long off = 0;
-  for (int s = 0; s < p.strips; ++s) {
-    p.col_off[s] = off;
-    const long long first_col = (long long)(s + 1) * R;  // column side starts here
-    if (sym && first_col < M) off += M - first_col;
-    p.slot_lo[s] = sym ? ((s * R) / cols) * ng : 0;
+// Tensor-core work list of a batch. For each series: strips of 128 - (L-1) output
+// rows; units of `tiles` Gram tiles (each yielding 256 - (L-1) output columns);
+// with the symmetric split only columns from each strip's own block on. Units
+// are ordered per series in groups of strips that run side by side (sharing A and
+// B tiles in L2), the groups from the last strip upwards. The band units (two
+// tiles of columns centred on each strip's rows) seed the row bounds first.
+void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
+                TcPlan& p) {
+  p.units.clear();
+  p.col_off.clear();
+  p.slot_lo.clear();
+  std::vector<WorkUnit> band;
+  int row_base = 0, out_base = 0, strip_base = 0;
+  long long part_base = 0, col_base = 0;
+  p.kmax = 0;
+  p.Lmax = 1;
+  p.table.n = B;
+  for (int b = 0; b < B; ++b) {
+    const int N = (int)sd[b].N, L = sd[b].L, k = sd[b].k;
+    const int M = N - L + 1;
+    const int R = kTileRows - (L - 1);
+    const int strips = (M + R - 1) / R;
+    const int cols = cols_opt > 0 ? cols_opt : tiles * (256 - (L - 1));
+    const int slots = (M + cols - 1) / cols;
+    SeriesInfo& si = p.table.s[b];
+    si.N = N;
+    si.M = M;
+    si.L = L;
+    si.k = k;
+    si.e = sd[b].e;
+    si.rows_out = R;
+    si.row_base = row_base;
+    si.out_base = out_base;
+    si.slots = slots;
+    si.strip_base = strip_base;
+    si.part_base = part_base;
+    si.col_base = col_base;
+    long long off = 0;
+    for (int s = 0; s < strips; ++s) {
+      p.col_off.push_back(off);
+      const long long first_col = (long long)(s + 1) * R;
+      if (sym && first_col < M) off += M - first_col;
+      p.slot_lo.push_back(sym ? (s * R) / cols : 0);
+    }
+    const int group = std::max(1, std::min(strips, 19));
+    const int ngroups = (strips + group - 1) / group;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const int g = sym ? ngroups - 1 - gi : gi;
+      const int s_lo = g * group, s_hi = std::min(strips, s_lo + group);
+      for (int c = 0; c < slots; ++c)
+        for (int s = s_lo; s < s_hi; ++s) {
+          int jlo = c * cols;
+          const int jhi = std::min(M, (c + 1) * cols);
+          if (sym) jlo = std::max(jlo, s * R);
+          if (jlo < jhi) p.units.push_back(WorkUnit{b, s, jlo, jhi, c, {0, 0, 0}});
+        }
+    }
+    const int bw = std::max(0, (2 * 256 - (L - 1) - R) / 2);
+    for (int s = 0; s < strips; ++s) {
+      const int T0 = s * R;
+      const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
+      if (jlo < jhi) band.push_back(WorkUnit{b, s, jlo, jhi, 0, {0, 0, 0}});
+    }
+    row_base += N;
+    out_base += M;
+    strip_base += strips;
+    part_base += (long long)M * slots;
+    col_base += off;
+    p.kmax = std::max(p.kmax, k);
+    p.Lmax = std::max(p.Lmax, L);
   }
-  p.col_lists = off;
-  const int ngroups = (p.strips + group - 1) / group;
-  for (int gi = 0; gi < ngroups; ++gi) {
-    const int g = sym ? ngroups - 1 - gi : gi;
-    const int s_lo = g * group, s_hi = std::min(p.strips, s_lo + group);
-    for (int c = 0; c < chunks; ++c)
-      for (int s = s_lo; s < s_hi; ++s) {
-        const int T0 = s * R;
-        int jlo = c * cols;
-        const int jhi = std::min(M, (c + 1) * cols);
-        if (sym) jlo = std::max(jlo, T0);
-        if (jlo >= jhi) continue;
-        p.units.push_back(WorkUnit{s, jlo, jhi, c});
-      }
-  }
-  // Band pre-pass: two tiles of columns centred on each strip's own rows. Its
-  // row-side lists are not kept; their k-th distances seed the row bounds that
-  // prune both sides of the main pass (candidates near in time first).
-  const int bw = std::max(0, (2 * 256 - (L - 1) - R) / 2);
-  for (int s = 0; s < p.strips; ++s) {
-    const int T0 = s * R;
-    const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
-    if (jlo < jhi) p.band.push_back(WorkUnit{s, jlo, jhi, 0});
-  }
-  return p;
+  p.nunits = (int)p.units.size();
+  p.nband = (int)band.size();
+  p.units.insert(p.units.end(), band.begin(), band.end());
+  p.rows = row_base;
+  p.out_rows = out_base;
+  p.part_lists = part_base;
+  p.col_lists = col_base;
 }
 
 traknn_status check_handle(traknn_handle h) {
   if (!h) return TRAKNN_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return TRAKNN_ERR_CUDA;
+  return TRAKNN_OK;
+}
+
+std::vector<int64_t> shape_key(const HostSeries* sd, int B, int64_t D, const traknn_ctx* h) {
+  std::vector<int64_t> key = {D, h->sym, h->unit_cols, (int64_t)h->precision, h->center, B};
+  for (int b = 0; b < B; ++b) {
+    key.push_back(sd[b].N);
+    key.push_back(sd[b].L);
+    key.push_back(sd[b].k);
+    key.push_back(sd[b].e);
+  }
+  return key;
+}
+
+// Device pointers of the tensor-core workspace for plan `p`.
+struct TcBuffers {
+  float* partial;
+  float* mu;
+  double* norms;
+  float* W;
+  void* hi;
+  void* lo;
+  float* part_d;
+  int32_t* part_i;
+  unsigned int* thr;
+  int32_t* col_n;
+  float* col_d;
+  int32_t* col_i;
+  int* counter;
+  int Dp;
+  size_t total;
+};
+
+TcBuffers tc_layout(const TcPlan& p, int64_t D, char* base) {
+  TcBuffers b;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    const size_t o = off;
+    off += bytes;
+    return base + o;
+  };
+  b.Dp = (int)align_up((size_t)D, 32);
+  const int B = p.table.n;
+  const size_t ks = (size_t)p.kmax;
+  b.partial = reinterpret_cast<float*>(take((size_t)B * kMeanSlices * D * sizeof(float)));
+  b.mu = reinterpret_cast<float*>(take((size_t)B * D * sizeof(float)));
+  b.norms = reinterpret_cast<double*>(take((size_t)p.rows * sizeof(double)));
+  b.W = reinterpret_cast<float*>(take((size_t)p.out_rows * sizeof(float)));
+  b.hi = take((size_t)p.rows * b.Dp * 2);
+  b.lo = take((size_t)p.rows * b.Dp * 2);
+  b.part_d = reinterpret_cast<float*>(take((size_t)p.part_lists * ks * sizeof(float)));
+  b.part_i = reinterpret_cast<int32_t*>(take((size_t)p.part_lists * ks * sizeof(int32_t)));
+  b.thr = reinterpret_cast<unsigned int*>(take((size_t)p.out_rows * sizeof(unsigned int)));
+  b.col_n = reinterpret_cast<int32_t*>(take((size_t)p.col_lists * sizeof(int32_t)));
+  b.col_d = reinterpret_cast<float*>(take((size_t)p.col_lists * ks * sizeof(float)));
+  b.col_i = reinterpret_cast<int32_t*>(take((size_t)p.col_lists * ks * sizeof(int32_t)));
+  b.counter = reinterpret_cast<int*>(take(256));
+  b.total = off;
+  return b;
+}
+
+// Make h->plan the plan for these series (built and uploaded when the shape changes)
+// and size the workspace. Must not run during a stream capture.
+traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
+                         cudaStream_t s, TcBuffers* out) {
+  std::vector<int64_t> key = shape_key(sd, B, D, h);
+  key.push_back(tiles);
+  TcPlan& p = h->plan;
+  if (p.key != key) {
+    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, p);
+    p.key = key;
+    const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
+    const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
+    const size_t sb = align_up(p.slot_lo.size() * sizeof(int), 256);
+    TRY_CUDA(cudaStreamSynchronize(s));  // earlier work may still read the old list
+    TRY_ST(ensure_buffer(h, &h->plan_dev, &h->plan_dev_bytes, ub + cb + sb));
+    char* pd = static_cast<char*>(h->plan_dev);
+    TRY_CUDA(cudaMemcpy(pd, p.units.data(), p.units.size() * sizeof(WorkUnit),
+                        cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(pd + ub, p.col_off.data(), p.col_off.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(pd + ub + cb, p.slot_lo.data(), p.slot_lo.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
+    drop_graphs(h);  // graphs captured the previous work list
+  }
+  for (int b = 0; b < B; ++b) {
+    p.table.s[b].X = sd[b].X;
+    p.table.s[b].idx = sd[b].idx;
+    p.table.s[b].dist = sd[b].dist;
+    p.table.s[b].score = sd[b].score;
+  }
+  const TcBuffers probe = tc_layout(p, D, nullptr);
+  TRY_ST(ensure_buffer(h, &h->tcws, &h->tcws_bytes, probe.total));
+  *out = tc_layout(p, D, static_cast<char*>(h->tcws));
+  return TRAKNN_OK;
+}
+
+// The launch sequence of one tensor-core call (also what a graph captures).
+traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D, bool even_aligned,
+                         cudaStream_t s, bool record_events) {
+  const TcPlan& p = h->plan;
+  const SeriesTable& sr = p.table;
+  const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
+  const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
+  char* pd = static_cast<char*>(h->plan_dev);
+
+  TcArgs a;
+  a.Dp = b.Dp;
+  a.rows = p.rows;
+  a.out_rows = p.out_rows;
+  a.Lmax = p.Lmax;
+  a.kmax = p.kmax;
+  a.W = b.W;
+  a.part_d = b.part_d;
+  a.part_i = b.part_i;
+  a.err = h->err;
+  a.wait_limit_ns = (long long)h->wait_limit_ms * 1000000LL;
+  a.debug_withhold = h->debug_withhold;
+
+  TcWork w;
+  w.units = reinterpret_cast<const WorkUnit*>(pd);
+  w.nunits = p.nunits;
+  w.kstride = p.kmax;
+  w.col_off = reinterpret_cast<const long long*>(pd + ub);
+  w.slot_lo = reinterpret_cast<const int*>(pd + ub + cb);
+  w.sym = h->sym;
+  w.col_d = b.col_d;
+  w.col_i = b.col_i;
+  w.col_n = b.col_n;
+  w.thr = b.thr;
+  w.counter = b.counter;
+  w.write_lists = 1;
+  w.stats = h->stats ? h->stats_dev : nullptr;
+
+  const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
+  TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
+  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, b.Dp, even_aligned, b.mu, b.hi, b.lo,
+                                    b.norms, s));
+  TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s));
+  TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
+  TRY_CUDA(cudaMemsetAsync(b.counter, 0, 2 * sizeof(int), s));
+  const int slot = h->ev_head;
+  if (record_events) TRY_CUDA(cudaEventRecord(h->ev_start[slot], s));
+  if (p.nband > 0) {
+    // threshold pre-pass over the band units (stored after the main units)
+    TcWork bw = w;
+    bw.units = w.units + p.nunits;
+    bw.nunits = p.nband;
+    bw.sym = 0;
+    bw.write_lists = 0;
+    bw.counter = w.counter + 1;
+    TRY_CUDA(launch_fused_tc(b.hi, b.lo, split, a, bw, sr, h->sm_count, s));
+  }
+  TRY_CUDA(launch_fused_tc(b.hi, b.lo, split, a, w, sr, h->sm_count, s));
+  if (record_events) {
+    TRY_CUDA(cudaEventRecord(h->ev_stop[slot], s));
+    h->ev_head = (h->ev_head + 1) % traknn_ctx::kRing;
+    h->ev_count = std::min(h->ev_count + 1, traknn_ctx::kRing);
+  }
+  TRY_CUDA(launch_merge_tc(a, w, sr, s));
+  h->launches += (h->center ? 2 : 1) + 2 + (p.nband > 0 ? 1 : 0) + 2;
+  return TRAKNN_OK;
+}
+
+bool inputs_even_aligned(const HostSeries* sd, int B, int64_t D) {
+  if (D % 2) return false;
+  for (int b = 0; b < B; ++b)
+    if (reinterpret_cast<uintptr_t>(sd[b].X) % 8) return false;
+  return true;
+}
+
+traknn_status validate_series(const HostSeries* sd, int B, int64_t D) {
+  if (B < 1) return TRAKNN_ERR_INVALID_ARG;
+  int64_t rows = 0;
+  for (int b = 0; b < B; ++b) {
+    if (!sd[b].X || !sd[b].idx || !sd[b].dist || !sd[b].score) return TRAKNN_ERR_INVALID_ARG;
+    TRY_ST(traknn_check_problem(sd[b].N, D, sd[b].L, sd[b].k, sd[b].e));
+    rows += sd[b].N;
+  }
+  if (rows > INT_MAX / 2) return TRAKNN_ERR_INVALID_ARG;
+  return TRAKNN_OK;
+}
+
+// Tiles per work unit for this batch shape: the autotuned value when tuning is on
+// (each candidate timed once after a warm-up launch, the fastest kept per shape),
+// else 16.
+traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
+                         int* tiles) {
+  *tiles = 16;
+  if (!h->autotune || h->unit_cols > 0) return TRAKNN_OK;
+  const std::vector<int64_t> key = shape_key(sd, B, D, h);
+  for (auto& t : h->tuned)
+    if (t.first == key) {
+      *tiles = t.second;
+      return TRAKNN_OK;
+    }
+  const bool even = inputs_even_aligned(sd, B, D);
+  cudaEvent_t e0, e1;
+  TRY_CUDA(cudaEventCreate(&e0));
+  TRY_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_t = 16;
+  for (int cand : {8, 16, 32}) {
+    TcBuffers buf;
+    TRY_ST(prepare_tc(h, sd, B, D, cand, s, &buf));
+    TRY_ST(enqueue_tc(h, buf, D, even, s, false));  // warm-up
+    TRY_CUDA(cudaEventRecord(e0, s));
+    TRY_ST(enqueue_tc(h, buf, D, even, s, false));
+    TRY_CUDA(cudaEventRecord(e1, s));
+    TRY_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_t = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned.emplace_back(key, best_t);
+  *tiles = best_t;
+  return TRAKNN_OK;
+}
+
+// Forward pass of B series on the tensor cores. With `graph` set the launch
+// sequence is captured once per (shape, pointers, options) and replayed.
+traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
+                     bool graph) {
+  if (!tc_available()) return TRAKNN_ERR_UNSUPPORTED;
+  int tiles = 16;
+  TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
+  TcBuffers buf;
+  TRY_ST(prepare_tc(h, sd, B, D, tiles, s, &buf));
+  const bool even = inputs_even_aligned(sd, B, D);
+  if (!graph) return enqueue_tc(h, buf, D, even, s, h->profile != 0);
+
+  std::vector<int64_t> key = h->plan.key;
+  for (int b = 0; b < B; ++b) {
+    key.push_back((int64_t)reinterpret_cast<uintptr_t>(sd[b].X));
+    key.push_back((int64_t)reinterpret_cast<uintptr_t>(sd[b].idx));
+    key.push_back((int64_t)reinterpret_cast<uintptr_t>(sd[b].dist));
+    key.push_back((int64_t)reinterpret_cast<uintptr_t>(sd[b].score));
+  }
+  key.push_back(h->stats);
+  key.push_back(h->debug_withhold);
+  key.push_back(h->wait_limit_ms);
+  for (auto& g : h->graphs)
+    if (g.key == key) {
+      TRY_CUDA(cudaGraphLaunch(g.exec, s));
+      h->launches += (h->center ? 2 : 1) + 2 + (h->plan.nband > 0 ? 1 : 0) + 2;
+      return TRAKNN_OK;
+    }
+  if (!h->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  // run once outside the capture (kernel attributes, first-use costs), then capture
+  TRY_ST(enqueue_tc(h, buf, D, even, s, false));
+  TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t l0 = h->launches;
+  TRY_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const traknn_status st = enqueue_tc(h, buf, D, even, h->cap_stream, false);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+  if (st != TRAKNN_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  TRY_CUDA(ce);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  TRY_CUDA(ie);
+  h->launches = l0;  // the capture enqueued nothing
+  h->graphs.push_back(GraphEntry{key, exec});
+  TRY_CUDA(cudaGraphLaunch(exec, s));
+  h->launches += (h->center ? 2 : 1) + 2 + (h->plan.nband > 0 ? 1 : 0) + 2;
   return TRAKNN_OK;
 }
 
@@ -257,7 +597,10 @@ traknn_status traknn_destroy(traknn_handle h) {
   if (!h) return TRAKNN_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ws) cudaFree(h->ws);
+  if (h->tcws) cudaFree(h->tcws);
   if (h->io) cudaFree(h->io);
   if (h->adj) cudaFree(h->adj);
   if (h->plan_dev) cudaFree(h->plan_dev);
@@ -299,6 +642,9 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
       if (v < 0 || v > (1 << 24)) return TRAKNN_ERR_INVALID_ARG;
       h->unit_cols = (int)v;
       return TRAKNN_OK;
+    case TRAKNN_OPT_AUTOTUNE:
+      h->autotune = v ? 1 : 0;
+      return TRAKNN_OK;
     case TRAKNN_OPT_STATS:
       if (v && !h->stats_dev) {
         if (cudaSetDevice(h->device) != cudaSuccess) return TRAKNN_ERR_CUDA;
@@ -326,77 +672,26 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
 traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int64_t D, int L,
                                 int k, int e, int32_t* nbr_idx, float* nbr_dist, float* score,
                                 void* stream) {
-  traknn_status st = check_handle(h);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(check_handle(h));
   if (!X || !nbr_idx || !nbr_dist || !score) return TRAKNN_ERR_INVALID_ARG;
-  st = traknn_check_problem(N, D, L, k, e);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(traknn_check_problem(N, D, L, k, e));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->precision != TRAKNN_PREC_FP32) {
+    const HostSeries sd{X, N, L, k, e, nbr_idx, nbr_dist, score};
+    return run_tc(h, &sd, 1, D, s, false);
+  }
+
+  // plain FP32 CUDA-core path
   const int M = (int)(N - L + 1);
-
-  const bool tc = h->precision != TRAKNN_PREC_FP32;
-  if (tc && !tc_available()) return TRAKNN_ERR_UNSUPPORTED;
-  Schedule sch = make_schedule(M, L, k, e, h->sm_count, h->col_chunks);
-
-  // tensor-core work list (rebuilt when the shape changes)
-  auto& pl = h->plan;
-  if (tc && (pl.M != M || pl.L != L || pl.k != k || pl.e != e || pl.sym != h->sym ||
-             pl.cols != h->unit_cols)) {
-    TcPlan tp = make_tc_plan(M, L, k, h->sym, h->unit_cols, h->sm_count);
-    const size_t nb = tp.band.size();
-    tp.units.insert(tp.units.end(), tp.band.begin(), tp.band.end());  // band units last
-    const size_t ub = align_up(tp.units.size() * sizeof(WorkUnit), 256);
-    const size_t cb = align_up(tp.col_off.size() * sizeof(long long), 256);
-    const size_t sb = align_up(tp.slot_lo.size() * sizeof(int), 256);
-    if (h->plan_dev && h->plan_dev_bytes < ub + cb + sb) TRY_CUDA(cudaStreamSynchronize(s));
-    st = ensure_buffer(&h->plan_dev, &h->plan_dev_bytes, ub + cb + sb);
-    if (st != TRAKNN_OK) return st;
-    char* pd = static_cast<char*>(h->plan_dev);
-    TRY_CUDA(cudaMemcpyAsync(pd, tp.units.data(), tp.units.size() * sizeof(WorkUnit),
-                             cudaMemcpyHostToDevice, s));
-    TRY_CUDA(cudaMemcpyAsync(pd + ub, tp.col_off.data(), tp.col_off.size() * sizeof(long long),
-                             cudaMemcpyHostToDevice, s));
-    TRY_CUDA(cudaMemcpyAsync(pd + ub + cb, tp.slot_lo.data(), tp.slot_lo.size() * sizeof(int),
-                             cudaMemcpyHostToDevice, s));
-    pl.M = M;
-    pl.L = L;
-    pl.k = k;
-    pl.e = e;
-    pl.sym = h->sym;
-    pl.cols = h->unit_cols;
-    pl.strips = tp.strips;
-    pl.slots = tp.slots;
-    pl.nunits = (int)(tp.units.size() - nb);
-    pl.nband = (int)nb;
-    pl.col_lists = tp.col_lists;
-    pl.bytes = ub;  // device layout: units | col_off | slot_lo
-  }
-  if (tc) sch.chunks = pl.slots;  // partial lists: one slot per column range
-
-  Layout lay = make_layout(N, D, sch);
-  size_t thr_off = 0, coln_off = 0, cold_off = 0, coli_off = 0, cnt_off = 0;
-  if (tc) {
-    auto take = [&](size_t bytes) {
-      lay.total = align_up(lay.total, 256);
-      size_t o = lay.total;
-      lay.total += bytes;
-      return o;
-    };
-    thr_off = take((size_t)M * sizeof(unsigned int));
-    coln_off = take((size_t)pl.col_lists * sizeof(int32_t));
-    cold_off = take((size_t)pl.col_lists * k * sizeof(float));
-    coli_off = take((size_t)pl.col_lists * k * sizeof(int32_t));
-    cnt_off = take(256);
-  }
-  st = ensure_buffer(&h->ws, &h->ws_bytes, lay.total);
-  if (st != TRAKNN_OK) return st;
+  const Schedule sch = make_schedule(M, L, k, e, h->sm_count, h->col_chunks);
+  const Layout lay = make_layout(N, D, sch);
+  TRY_ST(ensure_buffer(h, &h->ws, &h->ws_bytes, lay.total));
   char* ws = static_cast<char*>(h->ws);
   float* partial = reinterpret_cast<float*>(ws + lay.partial);
   float* mu = reinterpret_cast<float*>(ws + lay.mu);
   double* norms = reinterpret_cast<double*>(ws + lay.norms);
   float* W = reinterpret_cast<float*>(ws + lay.W);
-  void* ops = ws + lay.ops;
-
+  float* Xc = reinterpret_cast<float*>(ws + lay.ops);
   FusedArgs fa;
   fa.sch = sch;
   fa.N = (int)N;
@@ -407,96 +702,63 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   fa.err = h->err;
   fa.wait_limit_ns = (long long)h->wait_limit_ms * 1000000LL;
   fa.debug_withhold = h->debug_withhold;
-
-  TcWork tw;
-  if (tc) {
-    char* pd = static_cast<char*>(h->plan_dev);
-    const size_t ub = pl.bytes;
-    const size_t cb = align_up((size_t)pl.strips * sizeof(long long), 256);
-    tw.units = reinterpret_cast<const WorkUnit*>(pd);
-    tw.nunits = pl.nunits;
-    tw.slots = pl.slots;
-    tw.col_off = reinterpret_cast<const long long*>(pd + ub);
-    tw.slot_lo = reinterpret_cast<const int*>(pd + ub + cb);
-    tw.sym = h->sym;
-    tw.thr = reinterpret_cast<unsigned int*>(ws + thr_off);
-    tw.col_n = reinterpret_cast<int32_t*>(ws + coln_off);
-    tw.col_d = reinterpret_cast<float*>(ws + cold_off);
-    tw.col_i = reinterpret_cast<int32_t*>(ws + coli_off);
-    tw.counter = reinterpret_cast<int*>(ws + cnt_off);
-    tw.write_lists = 1;
-    tw.stats = h->stats ? h->stats_dev : nullptr;
-  }
-
   TRY_CUDA(launch_col_mean(X, (int)N, (int)D, partial, mu, h->center != 0, s));
-  h->launches += h->center ? 2 : 1;
-  const int slot = h->ev_head;
-  void* hi = ops;
-  void* lo = static_cast<char*>(ops) + (size_t)N * lay.Dp * 2;
-  if (!tc)
-    TRY_CUDA(launch_prep_fp32(X, (int)N, (int)D, lay.Dp, mu, static_cast<float*>(ops), norms, s));
-  else
-    TRY_CUDA(launch_prep_split(X, (int)N, (int)D, lay.Dp, mu, hi, lo, norms, s));
+  TRY_CUDA(launch_prep_fp32(X, (int)N, (int)D, lay.Dp, mu, Xc, norms, s));
   TRY_CUDA(launch_window(norms, M, L, W, s));
-  if (tc) {
-    TRY_CUDA(cudaMemsetAsync(tw.thr, 0x7F, (size_t)M * sizeof(unsigned int), s));
-    TRY_CUDA(cudaMemsetAsync(tw.counter, 0, 2 * sizeof(int), s));
-  }
+  const int slot = h->ev_head;
   if (h->profile) TRY_CUDA(cudaEventRecord(h->ev_start[slot], s));
-  if (!tc) {
-    TRY_CUDA(launch_fused_fp32(static_cast<float*>(ops), fa, h->sm_count, s));
-  } else {
-    const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
-    if (pl.nband > 0) {
-      // threshold pre-pass over the band units (stored after the main units)
-      TcWork bw = tw;
-      bw.units = tw.units + pl.nunits;
-      bw.nunits = pl.nband;
-      bw.sym = 0;
-      bw.write_lists = 0;
-      bw.counter = tw.counter + 1;
-      TRY_CUDA(launch_fused_tc(hi, lo, split, fa, bw, h->sm_count, s));
-      h->launches += 1;
-    }
-    TRY_CUDA(launch_fused_tc(hi, lo, split, fa, tw, h->sm_count, s));
-  }
+  TRY_CUDA(launch_fused_fp32(Xc, fa, h->sm_count, s));
   if (h->profile) {
     TRY_CUDA(cudaEventRecord(h->ev_stop[slot], s));
     h->ev_head = (h->ev_head + 1) % traknn_ctx::kRing;
     h->ev_count = std::min(h->ev_count + 1, traknn_ctx::kRing);
   }
-  if (!tc)
-    TRY_CUDA(launch_merge(fa, nbr_idx, nbr_dist, score, s));
-  else
-    TRY_CUDA(launch_merge_tc(fa, tw, nbr_idx, nbr_dist, score, s));
-  h->launches += 4;
+  TRY_CUDA(launch_merge(fa, nbr_idx, nbr_dist, score, s));
+  h->launches += (h->center ? 2 : 1) + 4;
+  return TRAKNN_OK;
+}
+
+traknn_status traknn_knn_scores_batched(traknn_handle h, const traknn_series* series, int B,
+                                        int64_t D, void* stream) {
+  TRY_ST(check_handle(h));
+  if (!series || B < 1 || D < 1) return TRAKNN_ERR_INVALID_ARG;
+  std::vector<HostSeries> sd(B);
+  for (int b = 0; b < B; ++b)
+    sd[b] = HostSeries{series[b].X, series[b].N, series[b].L, series[b].k, series[b].exclusion,
+                       series[b].nbr_idx, series[b].nbr_dist, series[b].score};
+  TRY_ST(validate_series(sd.data(), B, D));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->precision == TRAKNN_PREC_FP32) {
+    for (int b = 0; b < B; ++b)
+      TRY_ST(traknn_knn_scores(h, sd[b].X, sd[b].N, D, sd[b].L, sd[b].k, sd[b].e, sd[b].idx,
+                               sd[b].dist, sd[b].score, stream));
+    return TRAKNN_OK;
+  }
+  for (int b0 = 0; b0 < B; b0 += kMaxSeries)
+    TRY_ST(run_tc(h, sd.data() + b0, std::min(kMaxSeries, B - b0), D, s, true));
   return TRAKNN_OK;
 }
 
 traknn_status traknn_knn_scores_host(traknn_handle h, const float* Xh, int64_t N, int64_t D,
                                      int L, int k, int e, int32_t* idx_h, float* dist_h,
                                      float* score_h, void* stream) {
-  traknn_status st = check_handle(h);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(check_handle(h));
   if (!Xh || !idx_h || !dist_h || !score_h) return TRAKNN_ERR_INVALID_ARG;
-  st = traknn_check_problem(N, D, L, k, e);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(traknn_check_problem(N, D, L, k, e));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t M = N - L + 1;
   const size_t xb = align_up((size_t)N * D * sizeof(float), 256);
   const size_t ib = align_up((size_t)M * k * sizeof(int32_t), 256);
   const size_t db = align_up((size_t)M * k * sizeof(float), 256);
   const size_t sb = align_up((size_t)M * sizeof(float), 256);
-  st = ensure_buffer(&h->io, &h->io_bytes, xb + ib + db + sb);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(ensure_buffer(h, &h->io, &h->io_bytes, xb + ib + db + sb));
   char* io = static_cast<char*>(h->io);
   float* Xd = reinterpret_cast<float*>(io);
   int32_t* idx_d = reinterpret_cast<int32_t*>(io + xb);
   float* dist_d = reinterpret_cast<float*>(io + xb + ib);
   float* score_d = reinterpret_cast<float*>(io + xb + ib + db);
   TRY_CUDA(cudaMemcpyAsync(Xd, Xh, (size_t)N * D * sizeof(float), cudaMemcpyHostToDevice, s));
-  st = traknn_knn_scores(h, Xd, N, D, L, k, e, idx_d, dist_d, score_d, stream);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(traknn_knn_scores(h, Xd, N, D, L, k, e, idx_d, dist_d, score_d, stream));
   TRY_CUDA(cudaMemcpyAsync(idx_h, idx_d, (size_t)M * k * sizeof(int32_t),
                            cudaMemcpyDeviceToHost, s));
   TRY_CUDA(cudaMemcpyAsync(dist_h, dist_d, (size_t)M * k * sizeof(float),
@@ -510,15 +772,13 @@ traknn_status traknn_knn_scores_host(traknn_handle h, const float* Xh, int64_t N
 traknn_status traknn_score_backward(traknn_handle h, const float* X, int64_t N, int64_t D, int L,
                                     int k, const int32_t* nbr_idx, const float* grad_score,
                                     float* dX, void* stream) {
-  traknn_status st = check_handle(h);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(check_handle(h));
   if (!X || !nbr_idx || !grad_score || !dX) return TRAKNN_ERR_INVALID_ARG;
   if (N < 1 || D < 1 || L < 1 || L > N || k < 1) return TRAKNN_ERR_INVALID_ARG;
   if (N > INT_MAX / 2 || D > INT_MAX / 2) return TRAKNN_ERR_INVALID_ARG;
   if (L > TRAKNN_MAX_L || k > TRAKNN_MAX_K) return TRAKNN_ERR_UNSUPPORTED;
   const int M = (int)(N - L + 1);
-  st = ensure_buffer(&h->adj, &h->adj_bytes, adjoint_workspace_bytes(M, k));
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(ensure_buffer(h, &h->adj, &h->adj_bytes, adjoint_workspace_bytes(M, k)));
   int launches = 0;
   TRY_CUDA(launch_adjoint(X, (int)N, (int)D, L, k, nbr_idx, grad_score, dX, h->adj, h->err,
                           static_cast<cudaStream_t>(stream), &launches));
@@ -527,8 +787,7 @@ traknn_status traknn_score_backward(traknn_handle h, const float* X, int64_t N, 
 }
 
 traknn_status traknn_sync_status(traknn_handle h, void* stream) {
-  traknn_status st = check_handle(h);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(check_handle(h));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY_CUDA(cudaStreamSynchronize(s));
   int flag = 0;
@@ -541,8 +800,7 @@ traknn_status traknn_sync_status(traknn_handle h, void* stream) {
 }
 
 traknn_status traknn_profile_read(traknn_handle h, float* ms, int max_n, int* n_out) {
-  traknn_status st = check_handle(h);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(check_handle(h));
   if (!n_out || (max_n > 0 && !ms)) return TRAKNN_ERR_INVALID_ARG;
   TRY_CUDA(cudaDeviceSynchronize());
   const int n = std::min(h->ev_count, std::max(max_n, 0));
@@ -557,8 +815,7 @@ traknn_status traknn_profile_read(traknn_handle h, float* ms, int max_n, int* n_
 }
 
 traknn_status traknn_stats_read(traknn_handle h, uint64_t* counters, int n) {
-  traknn_status st = check_handle(h);
-  if (st != TRAKNN_OK) return st;
+  TRY_ST(check_handle(h));
   if (!counters || n < 0) return TRAKNN_ERR_INVALID_ARG;
   unsigned long long buf[kStatCount] = {};
   if (h->stats_dev) {
