@@ -198,10 +198,14 @@ traknn_status traknn_profile_read(traknn_handle handle, float* ms, int max_n, in
 
 /* Event counters of the tensor-core kernel accumulated while TRAKNN_OPT_STATS was on
  * (diagnostics): [0] row-side list insertions, [1] column-side candidates,
- * [2] columns recomputed after a buffer overflow, [3] non-empty column lists,
+ * [2] reserved (always 0), [3] non-empty column lists,
  * [4] 32-column chunks processed, [5] MMA-thread cycles waiting for a free
  * accumulator, [6] MMA-thread cycles waiting for operands, [7] MMA-thread cycles
- * in total (all summed over CTAs). Synchronises the device and resets them. */
+ * in total; cycles of the first epilogue thread [8] waiting for a filled
+ * accumulator, [9] loading a tile's window sums and column bounds, [10] reading
+ * out and staging chunks, [11] in the barrier after staging, [12] in the row-side
+ * scan up to the barrier after it, [13] in the column side, [14] in total (all
+ * summed over CTAs). Synchronises the device and resets them. */
 traknn_status traknn_stats_read(traknn_handle handle, uint64_t* counters, int n);
 
 /* Total number of kernels this handle has launched (all entry points). */

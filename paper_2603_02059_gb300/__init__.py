@@ -147,10 +147,11 @@ class Handle:
 
     def stats_read(self):
         """Kernel event counters since the last read (TRAKNN_OPT_STATS)."""
-        buf = (ctypes.c_uint64 * 8)()
-        _check(lib().traknn_stats_read(self._h, buf, 8), "stats_read")
-        names = ["row_inserts", "col_emits", "col_dense", "col_lists", "chunks",
-                 "mma_wait_tmem", "mma_wait_full", "mma_cycles"]
+        names = ["row_inserts", "col_emits", "reserved", "col_lists", "chunks",
+                 "mma_wait_tmem", "mma_wait_full", "mma_cycles", "epi_wait_acc",
+                 "epi_tile_head", "epi_stage", "epi_bar1", "epi_scan", "epi_col", "epi_cycles"]
+        buf = (ctypes.c_uint64 * len(names))()
+        _check(lib().traknn_stats_read(self._h, buf, len(names)), "stats_read")
         return {n: int(buf[i]) for i, n in enumerate(names)}
 
     def launch_count(self) -> int:

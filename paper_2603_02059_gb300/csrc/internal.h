@@ -142,13 +142,21 @@ struct TcArgs {
 enum : int {
   kStatRowInserts = 0,     // row-side list insertions
   kStatColEmits = 1,       // column-side candidates handed to a column
-  kStatColDense = 2,       // columns recomputed densely after a buffer overflow
+  kStatReserved = 2,       // reserved (always 0)
   kStatColLists = 3,       // non-empty column lists written
   kStatChunks = 4,         // 32-column chunks processed
   kStatMmaWaitTmem = 5,    // MMA-thread cycles spent waiting for a free accumulator
   kStatMmaWaitFull = 6,    // MMA-thread cycles spent waiting for a filled stage
   kStatMmaCycles = 7,      // MMA-thread cycles from start to end, summed over CTAs
-  kStatCount = 8
+  // epilogue phases, timed by its first thread (cycles, summed over CTAs)
+  kStatEpiWaitAcc = 8,     // waiting for a filled accumulator
+  kStatEpiTileHead = 9,    // per-tile loads of window sums and column bounds
+  kStatEpiStage = 10,      // TMEM read-out and staging of a chunk
+  kStatEpiBar1 = 11,       // barrier after staging (waits for the slowest thread)
+  kStatEpiScan = 12,       // row-side scan and emissions, to the barrier after them
+  kStatEpiCol = 13,        // column-side lists (and dense recomputation)
+  kStatEpiCycles = 14,     // epilogue first thread from start to end
+  kStatCount = 15
 };
 
 // ----------------------------------------------------------------- launchers

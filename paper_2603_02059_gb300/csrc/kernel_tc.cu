@@ -47,7 +47,6 @@ constexpr uint32_t kTileA = BM * KC * 2;  // bytes of one A operand tile
 constexpr uint32_t kTileB = BN * KC * 2;  // bytes of one B operand tile
 constexpr uint32_t kIdesc = ptx::idesc_bf16_f32(BM, BN);
 constexpr int kMaxStages = 8;
-constexpr int kColCap = 24;  // column-side candidates buffered per column and chunk
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
 
 // Sorted (ascending distance) list of the K best candidates of one row, held in
@@ -84,19 +83,10 @@ struct RegList {
   }
 };
 
-// True if (d, i) would enter the column list `cl` of column c (sorted by (d, i)),
-// whose k-th distance is ct.
-__device__ __forceinline__ bool key_before(float d, int32_t i, float ct, const SmemList& cl, int c) {
-  if (d < ct) return true;
-  if (d > ct) return false;
-  return i < cl.i[(cl.k - 1) * cl.stride + c];
-}
-
 // Shared memory of one epilogue group: Gram chunk with carried columns, W and row
-// bounds of a tile, column-side candidate buffers and counters, column lists.
+// bounds of a tile, W of the unit's rows, column-side row masks, column lists.
 __host__ __device__ constexpr size_t group_bytes(int k, int L) {
-  return (size_t)BM * chunk_pitch(L) * 4 + 2 * BN * 4 + 32 * kColCap * 8 + 64 * 4 +
-         (size_t)32 * k * 8;
+  return (size_t)BM * chunk_pitch(L) * 4 + 2 * BN * 4 + BM * 4 + 128 * 4 + (size_t)32 * k * 8;
 }
 
 // Bits [lo, hi) of a 32-bit word (empty when hi <= lo).
@@ -213,10 +203,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* Gbuf = reinterpret_cast<float*>(gptr);
   float* Wsh = Gbuf + BM * chunk_pitch(a.Lmax);  // window sums of the tile's output columns
   float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
-  float* Ed = Tsh + BN;          // [32][kColCap] column-side candidates: distance
-  int* Er = reinterpret_cast<int*>(Ed + 32 * kColCap);  // ... and accumulator row
-  int* ecount = Er + 32 * kColCap;  // [2][32] per-column counts, by chunk parity
-  float* Cld = reinterpret_cast<float*>(ecount + 64);  // [kmax][32] column-side lists
+  float* Wrow = Tsh + BN;        // [BM] window sums of the unit's rows
+  uint32_t* Cmask = reinterpret_cast<uint32_t*>(Wrow + BM);  // [4][32] column-side row masks
+  float* Cld = reinterpret_cast<float*>(Cmask + 128);  // [kmax][32] column-side lists
   int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * a.kmax);
   uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + gbytes);
   const uint32_t full0 = ptx::smem_u32(bars);
@@ -250,7 +239,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::mbar_init(qempty0 + 8u * i, 2);  // the MMA thread and the epilogue leader
     }
     *abort_flag = 0;
-    for (int i = 0; i < 64; ++i) ecount[i] = 0;
     ptx::fence_mbar_init();
     ptx::fence_proxy_async();
   }
@@ -416,17 +404,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int et = threadIdx.x - 64;  // 0..127 within the epilogue
     const int bar = 1;                // the epilogue's named barrier
     const int cx = ((warp - 2) & 3) * 8 + (lane & 7);      // column-side column of lanes 0..7
-    // the first chunk's emission counter was cleared at start-up; each chunk clears
-    // the other counter for its successor
     int qs = 0, gch = 0, gt = 0;
     uint32_t qphase = 0;
     bool ok = true;
     UnitSpan us;
+    // phase timing of the first epilogue thread (diagnostics)
+    const bool timed = w.stats != nullptr && et == 0;
+    long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
+    // event counts kept per thread, summed once at the end (diagnostics)
+    unsigned int cnt[5] = {0, 0, 0, 0, 0};
+    const long long e_start = timed ? clock64() : 0;
+    long long tp = e_start;
+    auto lap = [&](int i) {
+      if (timed) {
+        const long long now = clock64();
+        ph[i] += now - tp;
+        tp = now;
+      }
+    };
     RegList<K> list;
-    SmemList cl;
-    cl.d = Cld;
-    cl.i = Cli;
-    cl.stride = 32;
     while (ok) {
       bool wok = wait_bounded(qfull0 + 8u * qs, qphase, ctl);
       const int u = wok ? qval[qs] : 0;
@@ -444,14 +440,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!unit_span(w, p.sr.s, u, us)) continue;
       const int L = us.L;
       const int LDG = chunk_pitch(L);
-      cl.k = us.k;
       const int t = us.T0 + l;
       const bool row_ok = l < us.R && t < us.M;
       const float Wt = row_ok ? a.W[us.out_base + t] : 0.f;
       const int jsym = us.T0 + us.R;  // column side from here on (sym)
+      const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
+      Wrow[l] = Wt;  // read by the column side after the first tile's barrier
       list.reset();
       for (int it = 0; it < us.ntiles; ++it, ++gt) {
         const int acc = gt & 1;
+        lap(6);
         wok = wait_bounded(tfull0 + 8u * acc, (gt >> 1) & 1, ctl);
         wok = ptx::named_bar_and(bar, kEpiThreads, wok);  // all four warps agree
         if (!wok) {
@@ -459,6 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         ptx::tc_fence_after();
+        lap(0);
         const int c0 = us.jlo + it * (BN - (L - 1));
         // W and row bounds of this tile's output columns j = c0 - (L-1) + x (the
         // previous tile's readers passed its last barrier)
@@ -469,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           Tsh[x] = in ? __uint_as_float(__ldcg(w.thr + us.out_base + j)) : 0.f;
         }
         const float thr_row = row_ok ? __uint_as_float(__ldcg(w.thr + us.out_base + t)) : 0.f;
+        lap(1);
         // chunk ch+1 is read from TMEM while chunk ch is scanned
         uint32_t vr[32];
         ptx::tmem_ld32_async(tmem_base + lane_addr + (uint32_t)(acc * BN), vr);
@@ -487,16 +487,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::tc_fence_before();
             ptx::mbar_arrive(tempty0 + 8u * acc);
           }
+          lap(2);
           ptx::named_bar_sync(bar, kEpiThreads);
+          lap(3);
           const int j0 = c0 + ch * 32 - (L - 1);
-          const int eb = gch & 1;  // emission counters of this chunk
-          // clear the next chunk's counters (their last readers passed this barrier)
-          if (et < 32) ecount[(eb ^ 1) * 32 + et] = 0;
           // column side of this chunk: output columns j >= jsym inside the unit
           const uint32_t colrange = w.sym ? bit_range(max(jsym, us.jlo) - j0, us.jhi - j0) &
                                                 bit_range(ch == 0 ? L - 1 : 0, 32)
                                           : 0u;
-          const float thr_col = Tsh[ch * 32 + cx];
+          uint32_t ccand = 0;
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
             // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
@@ -515,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int x = 0; x < 32; ++x) c[x] += gm[x];
             }
             const float lthr = list.threshold();
-            uint32_t cand = 0, ccand = 0;
+            uint32_t cand = 0;
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
               const float dv = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);
@@ -524,83 +523,79 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             cand &= valid;
             ccand &= valid & colrange;
-            // recompute (identically) and hand out the few pairs that matter
-            while (cand | ccand) {
-              const uint32_t both = cand | ccand;
-              const int x = __ffs(both) - 1;
-              const uint32_t bit = 1u << x;
+            // recompute (identically) the few pairs that enter the row's list
+            while (cand) {
+              const int x = __ffs(cand) - 1;
+              cand &= cand - 1;
               float cc = g0[x];
               for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + x];
               const float dv = fmaxf(fmaf(-2.0f, cc, Wt + wv[x]), 0.0f);
-              if ((cand & bit) && dv < list.threshold() && dv <= thr_row) {
+              if (dv < list.threshold() && dv <= thr_row) {
                 list.insert(dv, j0 + x);
-                if (w.stats) atomicAdd(w.stats + kStatRowInserts, 1ull);
+                ++cnt[0];
               }
-              if (ccand & bit) {
-                const int pos = atomicAdd(ecount + eb * 32 + x, 1);
-                if (pos < kColCap) {
-                  Ed[x * kColCap + pos] = dv;
-                  Er[x * kColCap + pos] = l;
-                }
-                if (w.stats) atomicAdd(w.stats + kStatColEmits, 1ull);
-              }
-              cand &= ~bit;
-              ccand &= ~bit;
             }
           }
+          // column-side candidates, transposed by ballots: lane x of warp quadrant q
+          // holds the rows q*32 + b of column x that pass the column's bound
+          uint32_t cm = 0;
+          if (__any_sync(0xffffffffu, ccand != 0u)) {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+              const uint32_t b = __ballot_sync(0xffffffffu, (ccand >> x) & 1u);
+              cm = lane == x ? b : cm;
+            }
+            cnt[1] += __popc(ccand);
+          }
+          Cmask[q * 32 + lane] = cm;
           ptx::named_bar_sync(bar, kEpiThreads);
-          // every emission of this chunk happened before the barrier; a column that
-          // overflowed its buffer is recomputed densely from the resident Gram chunk
-          const int ne_lane = ecount[eb * 32 + lane];
-          const bool dense_any = __any_sync(0xffffffffu, ne_lane > kColCap);
+          lap(4);
           if (colrange && lane < 8 && ((colrange >> cx) & 1u)) {
-            // the column's candidates among the strip's rows, kept in (distance, row) order
+            // the column's list over the strip's rows: rows arrive in increasing
+            // order, so a strict compare keeps the smaller row first at equal
+            // distance ((distance, index) order)
             const int j = j0 + cx;
-            const long long li = us.col_base + w.col_off[us.strip_base + us.strip] + (j - jsym);
-            const int ne = ecount[eb * 32 + cx];
+            const float wj = Wsh[ch * 32 + cx];
             int n = 0;
-            float ct = CUDART_INF_F;
-            if (ne > 0) {
-              cl.reset(cx);
-              if (ne <= kColCap) {
-                for (int q2 = 0; q2 < ne; ++q2) {
-                  const float dv = Ed[cx * kColCap + q2];
-                  const int32_t tr = us.T0 + Er[cx * kColCap + q2];
-                  if (key_before(dv, tr, ct, cl, cx)) {
-                    ct = cl.insert_key(cx, dv, tr);
-                    ++n;
-                  }
+            for (int wq = 0; wq < 4; ++wq) {
+              uint32_t mk = Cmask[wq * 32 + cx];
+              while (mk) {
+                const int r = wq * 32 + __ffs(mk) - 1;
+                mk &= mk - 1;
+                const float* g0 = Gbuf + r * LDG;
+                float cc = g0[cx];
+                for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + cx];
+                const float dv = fmaxf(fmaf(-2.0f, cc, Wrow[r] + wj), 0.0f);
+                int pos;
+                if (n < us.k) {
+                  pos = n++;
+                } else if (dv < Cld[(us.k - 1) * 32 + cx]) {
+                  pos = us.k - 1;
+                } else {
+                  continue;
                 }
-              } else {
-                if (w.stats) atomicAdd(w.stats + kStatColDense, 1ull);
-                for (int r = 0; r < us.R; ++r) {
-                  const int tr = us.T0 + r;
-                  if (tr >= us.M || (tr > j ? tr - j : j - tr) <= us.e) continue;
-                  const float* g0 = Gbuf + r * LDG;
-                  float cc = g0[cx];
-                  for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + cx];
-                  const float dv =
-                      fmaxf(fmaf(-2.0f, cc, a.W[us.out_base + tr] + Wsh[ch * 32 + cx]), 0.0f);
-                  if (dv <= thr_col && dv < ct) {
-                    ct = cl.insert(cx, dv, tr);
-                    ++n;
-                  }
+                while (pos > 0 && Cld[(pos - 1) * 32 + cx] > dv) {
+                  Cld[pos * 32 + cx] = Cld[(pos - 1) * 32 + cx];
+                  Cli[pos * 32 + cx] = Cli[(pos - 1) * 32 + cx];
+                  --pos;
                 }
+                Cld[pos * 32 + cx] = dv;
+                Cli[pos * 32 + cx] = us.T0 + r;
               }
-              n = min(n, us.k);
-              if (w.stats && n > 0) atomicAdd(w.stats + kStatColLists, 1ull);
-              for (int pp = 0; pp < n; ++pp) {
-                w.col_d[li * w.kstride + pp] = cl.d[pp * 32 + cx];
-                w.col_i[li * w.kstride + pp] = cl.i[pp * 32 + cx];
-              }
+            }
+            const long long li = cbase + (j - jsym);
+            for (int pp = 0; pp < n; ++pp) {
+              w.col_d[li * w.kstride + pp] = Cld[pp * 32 + cx];
+              w.col_i[li * w.kstride + pp] = Cli[pp * 32 + cx];
             }
             w.col_n[li] = n;
-            if (n == us.k) atomicMin(w.thr + us.out_base + j, __float_as_uint(ct));
+            cnt[3] += n > 0;
+            if (n == us.k) atomicMin(w.thr + us.out_base + j, __float_as_uint(Cld[(n - 1) * 32 + cx]));
           }
-          // the dense path read other rows' Gram values and Wsh: keep them in place
-          // until it is done (uniform: every warp saw the same counters)
-          if (dense_any) ptx::named_bar_sync(bar, kEpiThreads);
-          if (w.stats && et == 0) atomicAdd(w.stats + kStatChunks, 1ull);
+          // the column side read other rows' Gram values: keep them until it is done
+          if (colrange) ptx::named_bar_sync(bar, kEpiThreads);
+          cnt[4] += et == 0;
+          lap(5);
           ++gch;
         }
         if (row_ok) {
@@ -619,6 +614,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+    }
+    if (w.stats) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        unsigned int v = cnt[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(w.stats + kStatRowInserts + i, (unsigned long long)v);
+      }
+    }
+    if (timed) {
+      lap(6);
+      for (int i = 0; i < 6; ++i) atomicAdd(w.stats + kStatEpiWaitAcc + i, (unsigned long long)ph[i]);
+      atomicAdd(w.stats + kStatEpiCycles, (unsigned long long)(clock64() - e_start));
     }
   }
 
