@@ -257,7 +257,8 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"independent series per rank x{ws}"},
         "fp32_path": None if ms_fp32 is None else {
             "value": aggregate(pairs, ms_fp32, ws), "ms_per_step": ms_fp32,
-            "kernel_ms": statistics.mean(kms_fp32) if kms_fp32 else None, "steps": fp32_steps},
+            "kernel_ms": statistics.mean(kms_fp32) if kms_fp32 else None, "steps": fp32_steps,
+            "roofline": fp32_roofline(N, D, kms_fp32, peaks)},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -269,6 +270,19 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return line
+
+
+def fp32_roofline(N, D, kms, peaks):
+    """FP32 CUDA-core path: both triangles of the Gram (N^2 x 2D flops) against the
+    FP32 FMA peak of 152 SMs at the maximum SM clock."""
+    if not kms:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = fp32_alu_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
+    ach = float(N) * N * 2 * D / (statistics.mean(kms) * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x sm_max_mhz"}
 
 
 def run_e2e(tk, h, X, L, k, e, prec, steps, ws, device):
@@ -307,6 +321,159 @@ def cpu_baseline(X, L, k, e, nrows):
             "kind": "oracle", "seconds": el,
             "sample": f"{nrows} evenly spaced trajectory rows x all M={M} candidates "
                       f"(FP64 direct differences, full sort)"}
+
+
+# ------------------------------------------------------------ extra workloads
+
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 partitions x 32)
+
+
+def fp32_alu_peak_tflops(sm_count: int, sm_mhz: float) -> float:
+    """FP32 FMA peak from unit counts and clock: SMs x lanes x 2 flops x clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _events_ms(fn, steps, warmup, stream=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def suite_precision(args):
+    """0.25-degree grid (D = 58,101), L in {3, 5, 7, 10}, k = 20: split-BF16 throughput
+    per L (the cost of the diagonal window must not grow with L) and the FP32 path
+    at L = 5."""
+    import torch
+
+    import paper_2603_02059_gb300 as tk
+    from synth import config_inputs
+    X, meta, cfg = config_inputs("euro_75y_181x321")
+    N, D = X.shape
+    Xd = torch.from_numpy(X).cuda()
+    del X
+    h = tk.get_handle()
+    peaks, src = measured_peaks()
+    out = []
+    for L in (3, 5, 7, 10):
+        k, e = cfg["k"], L - 1
+        M = N - L + 1
+        h.profile_read()
+        h.set_option("profile", 1)
+        ms = _events_ms(lambda: tk.knn_scores(Xd, L, k, e, handle=h), args.steps, 3)
+        kms = h.profile_read()[3:]
+        h.set_option("profile", 0)
+        kavg = statistics.mean(kms) if kms else None
+        flops = N * (N + 1) / 2 * 3 * 2 * D
+        ach = flops / (kavg * 1e-3) / 1e12 if kavg else None
+        out.append({"L": L, "k": k, "exclusion": e, "ms_per_step": ms,
+                    "pairs_per_s": float(M) * M / (ms * 1e-3), "kernel_ms": kavg,
+                    "tensor_tflops": ach,
+                    "frac_sustained": ach / peaks["bf16_tflops_sustained"] if ach else None,
+                    "frac_burst": ach / peaks["bf16_tflops"] if ach else None})
+    L, k = 5, cfg["k"]
+    M = N - L + 1
+    ms32 = _events_ms(lambda: tk.knn_scores(Xd, L, k, L - 1, precision="fp32", handle=h), 1, 1)
+    if h.sync_status() != 0:
+        raise RuntimeError("device-side failure")
+    return {"suite": "precision_sweep", "workload": f"euro_75y_181x321: N={N}, D={D}",
+            "split_bf16": out,
+            "fp32_L5": {"ms_per_step": ms32, "pairs_per_s": float(M) * M / (ms32 * 1e-3)},
+            "peak_source": src}
+
+
+def batched_shapes(n_series=64, seed=20260305):
+    """64 series of uneven length N ~ U[3650, 27394], L ~ U{2..10}, k in {5, 10, 20},
+    exclusion L - 1, all on the 46 x 81 grid."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    for _ in range(n_series):
+        N = int(rng.integers(3650, 27395))
+        L = int(rng.integers(2, 11))
+        k = int(rng.choice([5, 10, 20]))
+        shapes.append((N, L, k, L - 1))
+    return shapes
+
+
+def suite_batched(args):
+    """64 uneven series in one batched call (persistent launches replayed from a CUDA
+    graph, tiles per unit autotuned) against 64 sequential single-series calls."""
+    import torch
+
+    import paper_2603_02059_gb300 as tk
+    from synth import make_slp_like
+    shapes = batched_shapes()
+    Xs = []
+    for b, (N, L, k, e) in enumerate(shapes):
+        X, _ = make_slp_like(N, 46, 81, seed=20260400 + b)
+        Xs.append(torch.from_numpy(X).cuda())
+    h = tk.get_handle()
+    pairs = float(sum((N - L + 1) ** 2 for N, L, k, e in shapes))
+    outs = [(torch.empty((N - L + 1, k), dtype=torch.int32, device="cuda"),
+             torch.empty((N - L + 1, k), dtype=torch.float32, device="cuda"),
+             torch.empty((N - L + 1,), dtype=torch.float32, device="cuda"))
+            for N, L, k, e in shapes]
+    series = [(X, L, k, e) for X, (N, L, k, e) in zip(Xs, shapes)]
+
+    def seq():
+        for (X, L, k, e), o in zip(series, outs):
+            tk.knn_scores(X, L, k, e, handle=h, out=o)
+
+    def bat():
+        tk.knn_scores_batched(series, handle=h, outs=outs, autotune=True)
+
+    ms_seq = _events_ms(seq, args.steps, 3)
+    ms_bat = _events_ms(bat, args.steps, 3)
+    h.set_option("autotune", 0)
+    if h.sync_status() != 0:
+        raise RuntimeError("device-side failure")
+    return {"suite": "batched", "series": len(shapes), "D": 46 * 81,
+            "total_days": sum(s[0] for s in shapes), "pairs_per_step": pairs,
+            "batched": {"ms_per_step": ms_bat, "pairs_per_s": pairs / (ms_bat * 1e-3)},
+            "sequential": {"ms_per_step": ms_seq, "pairs_per_s": pairs / (ms_seq * 1e-3)},
+            "speedup": ms_seq / ms_bat}
+
+
+def suite_adjoint(args):
+    """30-year workload (N = 10,957, D = 3,726, L = 5, k = 10): forward pass and the
+    adjoint of the summed score; the adjoint is HBM-bound (bytes: read X, idx, g;
+    write dX)."""
+    import torch
+
+    import paper_2603_02059_gb300 as tk
+    from synth import config_inputs
+    X, meta, cfg = config_inputs("euro_30y_46x81")
+    N, D = X.shape
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    M = N - L + 1
+    Xd = torch.from_numpy(X).cuda()
+    h = tk.get_handle()
+    idx, dist, score = tk.knn_scores(Xd, L, k, e, handle=h)
+    g = torch.ones(M, device="cuda")
+    ms_fwd = _events_ms(lambda: tk.knn_scores(Xd, L, k, e, handle=h, out=(idx, dist, score)),
+                        args.steps, 3)
+    ms_bwd = _events_ms(lambda: tk.score_backward(Xd, L, k, idx, g, handle=h), args.steps, 3)
+    if h.sync_status() != 0:
+        raise RuntimeError("device-side failure")
+    peaks, src = measured_peaks()
+    algo = 2 * N * D * 4 + M * k * 4 + M * 4
+    gbs = algo / (ms_bwd * 1e-3) / 1e9
+    return {"suite": "adjoint", "workload": f"euro_30y_46x81: N={N}, D={D}, L={L}, k={k}",
+            "forward_ms": ms_fwd, "forward_pairs_per_s": float(M) * M / (ms_fwd * 1e-3),
+            "backward_ms": ms_bwd, "backward_algorithmic_bytes": algo,
+            "backward_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+            "frac": gbs / peaks["hbm_gbs"], "peak_source": src}
+
+
+SUITES = {"precision": suite_precision, "batched": suite_batched, "adjoint": suite_adjoint}
 
 
 # --------------------------------------------------------------- reference arm
@@ -357,10 +524,18 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true", help="do not time the FP32 path")
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
+    ap.add_argument("--suite", choices=sorted(SUITES) + ["all"], default=None,
+                    help="instead of the headline line, time the extra workloads "
+                         "(one JSON line each, one GPU)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     ws, rank, local = dist_env()
+    if args.suite:
+        names = sorted(SUITES) if args.suite == "all" else [args.suite]
+        for n in names:
+            print(json.dumps(SUITES[n](args)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, ws, rank)
     else:

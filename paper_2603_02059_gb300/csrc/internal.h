@@ -9,6 +9,12 @@ namespace traknn {
 
 // Rows of one Gram tile (the tcgen05 accumulator height and the FP32 SIMT tile).
 constexpr int kTileRows = 128;
+// Columns of one tensor-core Gram tile (one TMEM accumulator).
+constexpr int kTileCols = 256;
+// Default length (elements of K) of one tensor-core accumulation segment: the
+// tensor cores accumulate at most this many products per output before the
+// partial sum is added, in FP32 on the CUDA cores, to the tile's running total.
+constexpr int kSegmentK = 8192;
 // Left halo kept beside each G tile in shared memory: the diagonal window of
 // Eq. 2 reaches L-1 <= kHalo columns to the right of an output column.
 constexpr int kHalo = 16;
@@ -116,7 +122,7 @@ struct TcWork {
   const long long* col_off; // [stacked strips] column-list offset within the series
   const int* slot_lo;       // [stacked strips] first slot written for the strip's rows
   int sym;                  // 1: upper triangle + column side
-  float* col_d;             // [lists][kstride] column-side candidate distances (sorted)
+  float* col_d;             // [lists][kstride] column-side candidate distances (in row order)
   int32_t* col_i;           // [lists][kstride] column-side candidate rows
   int32_t* col_n;           // [lists] number of valid entries of each column list
   unsigned int* thr;        // [stacked rows] bit patterns of an upper bound of each row's k-th distance
@@ -136,7 +142,16 @@ struct TcArgs {
   int* err;
   long long wait_limit_ns;
   int debug_withhold;
+  int seg_k;           // elements of K per accumulation segment (multiple of 32)
+  int groups;          // K groups of the operand layout (see tc_groups)
+  const float* cval;   // [rows] correction value c of every stacked operand row
+  float* scratch;      // [CTAs][2][128 x 256] running tile totals (more than one segment)
 };
+
+// Bytes of TcArgs::scratch for a launch of `num_ctas` CTAs.
+inline size_t tc_scratch_bytes(int num_ctas) {
+  return (size_t)num_ctas * 2 * kTileRows * kTileCols * sizeof(float);
+}
 
 // Event counters of the tensor-core kernel (diagnostics, TRAKNN_OPT_STATS).
 enum : int {
@@ -180,9 +195,12 @@ cudaError_t launch_merge_tc(const TcArgs& a, const TcWork& w, const SeriesTable&
 // Series-aware preparation for the tensor-core path (stacked operands).
 cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial, float* mu,
                                    bool center, cudaStream_t st);
-cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int Dp,
-                                     bool even_aligned, const float* mu, void* hi, void* lo,
-                                     double* norms, cudaStream_t st);
+// Operand layout of the tensor-core path: groups = ceil(D / 63) groups of 64 K
+// entries (63 permuted grid points + 1 correction entry); pitch groups * 64.
+inline int tc_groups(int D) { return (D + 62) / 63; }
+cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int groups,
+                                     bool correct, const float* mu, void* hi, void* lo,
+                                     double* norms, float* cval, cudaStream_t st);
 cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
                                  float* W, cudaStream_t st);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,

@@ -13,7 +13,15 @@
 //   warp 0   TMA producer: A (128 strip rows) and B (256 tile columns) K-chunks of
 //            32 elements into a ring of shared-memory stages (hi and lo copies);
 //   warp 1   tcgen05.mma issuer into one of two 128 x 256 FP32 accumulators in
-//            TMEM (512 columns), so tile i+1 multiplies while tile i is scanned;
+//            TMEM (512 columns). The K range of a tile is cut into segments
+//            (8192 elements by default); every segment accumulates afresh into
+//            the next accumulator, so segment s+1 multiplies while segment s is
+//            read out. With more than one segment per tile the epilogue adds the
+//            segments in FP32 on the CUDA cores into a running total of the tile
+//            in a per-CTA scratch array (L2-resident) and scans the tile from
+//            there: the tensor cores never accumulate more than one segment of
+//            products per output, which bounds the error of their accumulation
+//            however large D is;
 //   warps 2-5 epilogue: each thread owns one accumulator row (TMEM lane), pulls
 //            32 columns at a time with tcgen05.ld, stages them beside the L-1
 //            columns carried from the previous chunk, and runs the shared
@@ -33,7 +41,7 @@ namespace traknn {
 namespace {
 
 constexpr int BM = kTileRows;  // accumulator rows (TMEM lanes)
-constexpr int BN = 256;        // accumulator columns per tile
+constexpr int BN = kTileCols;  // accumulator columns per tile (256)
 constexpr int KC = 32;         // K elements per stage (64 B rows, 64-B swizzle)
 constexpr int kEpiThreads = 128;  // one epilogue group: one thread per accumulator row
 // Threads of a CTA: warp 0 producer, warp 1 MMA issuer, four epilogue warps.
@@ -83,10 +91,10 @@ struct RegList {
   }
 };
 
-// Shared memory of one epilogue group: Gram chunk with carried columns, W and row
-// bounds of a tile, W of the unit's rows, column-side row masks, column lists.
+// Shared memory of one epilogue group: Gram chunk with carried columns, W, row
+// bounds and correction values of a tile, column-side row masks, column lists.
 __host__ __device__ constexpr size_t group_bytes(int k, int L) {
-  return (size_t)BM * chunk_pitch(L) * 4 + 2 * BN * 4 + BM * 4 + 128 * 4 + (size_t)32 * k * 8;
+  return (size_t)BM * chunk_pitch(L) * 4 + 3 * BN * 4 + 128 * 4 + (size_t)32 * k * 8;
 }
 
 // Bits [lo, hi) of a 32-bit word (empty when hi <= lo).
@@ -104,6 +112,7 @@ struct TcParams {
   int nstages;
   int split;
   uint32_t stage_bytes;
+  int seg_kb;  // K blocks (of KC elements) per accumulation segment
   SeriesTable sr;
 };
 
@@ -167,6 +176,15 @@ __device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr,
   return true;
 }
 
+// Publish an upper bound of a row's k-th distance. The same pair distance can be
+// evaluated more than once (band pre-pass and main pass; a pair and its transpose)
+// with results a few ulp apart, so a bound taken from one evaluation is widened by
+// a relative 2^-12 (far above those differences) before it prunes another; a wider
+// bound only admits more candidates to the exact final selection.
+__device__ __forceinline__ void publish_bound(unsigned int* thr, float d) {
+  atomicMin(thr, __float_as_uint(__fmul_ru(d, 1.0f + 0x1p-12f)));
+}
+
 // The k-th entry of a sorted register list (k is a run-time value, K a compile-time
 // bound): the minimum of entries k-1 .. K-1, written as a reduction so that the
 // list stays in registers.
@@ -203,8 +221,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* Gbuf = reinterpret_cast<float*>(gptr);
   float* Wsh = Gbuf + BM * chunk_pitch(a.Lmax);  // window sums of the tile's output columns
   float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
-  float* Wrow = Tsh + BN;        // [BM] window sums of the unit's rows
-  uint32_t* Cmask = reinterpret_cast<uint32_t*>(Wrow + BM);  // [4][32] column-side row masks
+  float* Csh = Tsh + BN;         // correction values c of the tile's Gram columns
+  uint32_t* Cmask = reinterpret_cast<uint32_t*>(Csh + BN);  // [4][32] column-side row masks
   float* Cld = reinterpret_cast<float*>(Cmask + 128);  // [kmax][32] column-side lists
   int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * a.kmax);
   uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + gbytes);
@@ -238,6 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::mbar_init(qfull0 + 8u * i, 1);
       ptx::mbar_init(qempty0 + 8u * i, 2);  // the MMA thread and the epilogue leader
     }
+
     *abort_flag = 0;
     ptx::fence_mbar_init();
     ptx::fence_proxy_async();
@@ -251,6 +270,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int nkb = a.Dp / KC;
+  const int seg_kb = p.seg_kb;                    // K blocks per accumulation segment
+  const int nseg = (nkb + seg_kb - 1) / seg_kb;   // segments per tile
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -318,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int stage = 0, qs = 0, gt = 0;
+      int stage = 0, qs = 0, gt = 0, gs = 0, acc = 0;  // gs: segments issued so far
       uint32_t phase = 0, qphase = 0;
       bool ok = true, issued_any = false;
       long long wait_tmem = 0, wait_full = 0;
@@ -338,17 +359,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (u >= w.nunits) break;
         if (!unit_span(w, p.sr.s, u, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it, ++gt) {
-          // tile gt uses accumulator gt & 1 for the (gt >> 1)-th time
-          const int acc = gt & 1;
-          const long long tw0 = w.stats ? clock64() : 0;
-          if (!wait_bounded(tempty0 + 8u * acc, ((gt >> 1) & 1) ^ 1u, ctl)) {
-            ok = false;
-            break;
-          }
-          if (w.stats) wait_tmem += clock64() - tw0;
-          ptx::tc_fence_after();
-          const uint32_t d = tmem_base + (uint32_t)(acc * BN);
           for (int kb = 0; kb < nkb; ++kb) {
+            if (kb % seg_kb == 0) {
+              // a new segment: segment gs uses accumulator gs & 1 for the (gs >> 1)-th time
+              if (kb > 0) {
+                ptx::mma_commit(tfull0 + 8u * acc);  // the finished segment to the epilogue
+                ++gs;
+              }
+              acc = gs & 1;
+              const long long tw0 = w.stats ? clock64() : 0;
+              if (!wait_bounded(tempty0 + 8u * acc, ((gs >> 1) & 1) ^ 1u, ctl)) {
+                ok = false;
+                break;
+              }
+              if (w.stats) wait_tmem += clock64() - tw0;
+              ptx::tc_fence_after();
+            }
+            const uint32_t d = tmem_base + (uint32_t)(acc * BN);
             const long long tf0 = w.stats ? clock64() : 0;
             if (!wait_bounded(full0 + 8u * stage, phase, ctl)) {
               ok = false;
@@ -361,11 +388,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_lo = sb + kTileA;
             const uint32_t b_hi = p.split ? sb + 2 * kTileA : sb + kTileA;
             const uint32_t b_lo = b_hi + kTileB;
+            const uint32_t first = kb % seg_kb == 0 ? 1u : 0u;
 #pragma unroll
             for (int kk = 0; kk < KC / 16; ++kk) {
               const uint64_t dah = ptx::sdesc_kmajor_sw64(a_hi + kk * 32);
               const uint64_t dbh = ptx::sdesc_kmajor_sw64(b_hi + kk * 32);
-              ptx::mma_f16(d, dah, dbh, kIdesc, (kb | kk) != 0);
+              ptx::mma_f16(d, dah, dbh, kIdesc, (first && kk == 0) ? 0u : 1u);
               if (p.split) {
                 const uint64_t dal = ptx::sdesc_kmajor_sw64(a_lo + kk * 32);
                 const uint64_t dbl = ptx::sdesc_kmajor_sw64(b_lo + kk * 32);
@@ -381,7 +409,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           if (!ok) break;
-          ptx::mma_commit(tfull0 + 8u * acc);  // accumulator ready for the epilogue
+          ptx::mma_commit(tfull0 + 8u * acc);  // the tile's last segment
+          ++gs;
         }
       }
       if (w.stats) {
@@ -423,6 +452,71 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     RegList<K> list;
+    // Segment folding (more than one segment per tile): segment pseg of tile pt is
+    // the next to add to the tile's partial total; every segment but a tile's last
+    // is folded (segment s of tile t is segment t * nseg + s overall, in accumulator
+    // (t * nseg + s) & 1), the last is added while the tile is scanned. The partial
+    // totals live in this CTA's scratch array, two tile slots of
+    // [8 chunks][8 float4 groups][128 rows] float4; each thread folds and later
+    // reads only its own row, so warps fold independently.
+    int pt = 0, pseg = 0;
+    long long fold_cycles = 0;
+    float4* const scr = reinterpret_cast<float4*>(a.scratch) + (size_t)blockIdx.x * (2 * BM * BN / 4);
+    auto fold = [&](bool block, int upto) -> bool {
+      while (nseg > 1 && pt <= upto) {
+        const long long gsi = (long long)pt * nseg + pseg;
+        const int b = (int)(gsi & 1);
+        const uint32_t par = (uint32_t)((gsi >> 1) & 1);
+        if (!block) {
+          const bool r = ptx::mbar_try_wait(tfull0 + 8u * b, par);
+          if (!__shfl_sync(0xffffffffu, r, 0)) return true;  // not ready: try later
+        }
+        if (!wait_bounded(tfull0 + 8u * b, par, ctl)) return false;
+        const long long f0 = timed ? clock64() : 0;
+        ptx::tc_fence_after();
+        const uint32_t tA = tmem_base + lane_addr + (uint32_t)(b * BN);
+        float4* srow = scr + (size_t)(pt & 1) * (BM * BN / 4) + l;
+        // the first segment is stored, later ones are added by FP32 reductions in L2
+        // (round to nearest); every element has this thread as its only writer, so
+        // the additions happen in segment order and the total is deterministic
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t v[32];
+          ptx::tmem_ld32_async(tA + c * 32, v);
+          ptx::tmem_wait();
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const float4 r = make_float4(__uint_as_float(v[4 * g]), __uint_as_float(v[4 * g + 1]),
+                                         __uint_as_float(v[4 * g + 2]),
+                                         __uint_as_float(v[4 * g + 3]));
+            if (pseg == 0)
+              __stcg(srow + (c * 8 + g) * BM, r);
+            else
+              atomicAdd(srow + (c * 8 + g) * BM, r);
+          }
+        }
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(tempty0 + 8u * b);  // the accumulator is free for the next segment
+        if (timed) fold_cycles += clock64() - f0;
+        if (++pseg == nseg - 1) {
+          pseg = 0;
+          ++pt;
+        }
+      }
+      return true;
+    };
+    // 32 columns (chunk ch) of this thread's row of tile gt's total, from the scratch
+    auto load_scr = [&](int tile, int ch, uint32_t (&v)[32]) {
+      const float4* srow = scr + (size_t)(tile & 1) * (BM * BN / 4) + l;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const float4 r = __ldcg(srow + (ch * 8 + g) * BM);
+        v[4 * g] = __float_as_uint(r.x);
+        v[4 * g + 1] = __float_as_uint(r.y);
+        v[4 * g + 2] = __float_as_uint(r.z);
+        v[4 * g + 3] = __float_as_uint(r.w);
+      }
+    };
     while (ok) {
       bool wok = wait_bounded(qfull0 + 8u * qs, qphase, ctl);
       const int u = wok ? qval[qs] : 0;
@@ -443,14 +537,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int t = us.T0 + l;
       const bool row_ok = l < us.R && t < us.M;
       const float Wt = row_ok ? a.W[us.out_base + t] : 0.f;
+      // the operand layout subtracts groups * c_a * c_b from every Gram entry (see the
+      // operand preparation); it is added back when a chunk is staged, for every
+      // accumulator row whose day exists (halo rows feed other rows' windows)
+      const int N = us.M + us.L - 1;
+      const float crow = t < N ? (float)a.groups * a.cval[us.row_base + t] : 0.f;
       const int jsym = us.T0 + us.R;  // column side from here on (sym)
       const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
-      Wrow[l] = Wt;  // read by the column side after the first tile's barrier
       list.reset();
       for (int it = 0; it < us.ntiles; ++it, ++gt) {
-        const int acc = gt & 1;
         lap(6);
-        wok = wait_bounded(tfull0 + 8u * acc, (gt >> 1) & 1, ctl);
+        // the earlier segments are folded into the scratch partial total; the last
+        // one is read from its accumulator while the tile is scanned
+        // accumulator holding the tile's last segment (the whole tile if nseg == 1)
+        const long long glast = (long long)gt * nseg + nseg - 1;
+        const int acc_l = (int)(glast & 1);
+        if (nseg > 1) wok = fold(true, gt);
+        if (wok) wok = wait_bounded(tfull0 + 8u * acc_l, (uint32_t)((glast >> 1) & 1), ctl);
         wok = ptx::named_bar_and(bar, kEpiThreads, wok);  // all four warps agree
         if (!wok) {
           ok = false;
@@ -466,26 +569,50 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool in = j >= 0 && j < us.M;
           Wsh[x] = in ? a.W[us.out_base + j] : 0.f;
           Tsh[x] = in ? __uint_as_float(__ldcg(w.thr + us.out_base + j)) : 0.f;
+          Csh[x] = c0 + x < N ? a.cval[us.row_base + c0 + x] : 0.f;  // Gram column day c0 + x
         }
         const float thr_row = row_ok ? __uint_as_float(__ldcg(w.thr + us.out_base + t)) : 0.f;
+        ptx::named_bar_sync(bar, kEpiThreads);  // Csh is read by every thread when staging
         lap(1);
-        // chunk ch+1 is read from TMEM while chunk ch is scanned
+        // chunk ch+1 is fetched while chunk ch is scanned: from TMEM with a single
+        // segment, else the scratch partial total (the last segment's chunk is
+        // added from TMEM when the chunk is staged)
+        const uint32_t tlast = tmem_base + lane_addr + (uint32_t)(acc_l * BN);
         uint32_t vr[32];
-        ptx::tmem_ld32_async(tmem_base + lane_addr + (uint32_t)(acc * BN), vr);
+        if (nseg == 1)
+          ptx::tmem_ld32_async(tlast, vr);
+        else
+          load_scr(gt, 0, vr);
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
-          ptx::tmem_wait();
           float* grow = Gbuf + l * LDG;
           if (ch > 0)
             for (int c = 0; c < L - 1; ++c) grow[c] = grow[32 + c];
+          const float* cs = Csh + ch * 32;
+          if (nseg == 1) {
+            ptx::tmem_wait();
 #pragma unroll
-          for (int x = 0; x < 32; ++x) grow[(L - 1) + x] = __uint_as_float(vr[x]);
-          if (ch + 1 < BN / 32)
-            ptx::tmem_ld32_async(tmem_base + lane_addr + (uint32_t)(acc * BN + (ch + 1) * 32), vr);
+            for (int x = 0; x < 32; ++x)
+              grow[(L - 1) + x] = fmaf(crow, cs[x], __uint_as_float(vr[x]));
+          } else {
+            uint32_t tv[32];
+            ptx::tmem_ld32_async(tlast + (uint32_t)(ch * 32), tv);
+            ptx::tmem_wait();
+#pragma unroll
+            for (int x = 0; x < 32; ++x)
+              grow[(L - 1) + x] =
+                  fmaf(crow, cs[x], __uint_as_float(vr[x]) + __uint_as_float(tv[x]));
+          }
+          if (ch + 1 < BN / 32) {
+            if (nseg == 1)
+              ptx::tmem_ld32_async(tlast + (uint32_t)((ch + 1) * 32), vr);
+            else
+              load_scr(gt, ch + 1, vr);
+          }
           if (ch == BN / 32 - 1) {
             // the accumulator has been read out: hand it back to the MMA warp
             ptx::tc_fence_before();
-            ptx::mbar_arrive(tempty0 + 8u * acc);
+            ptx::mbar_arrive(tempty0 + 8u * acc_l);
           }
           lap(2);
           ptx::named_bar_sync(bar, kEpiThreads);
@@ -495,7 +622,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t colrange = w.sym ? bit_range(max(jsym, us.jlo) - j0, us.jhi - j0) &
                                                 bit_range(ch == 0 ? L - 1 : 0, 32)
                                           : 0u;
-          uint32_t ccand = 0;
+          uint32_t cand = 0, ccand = 0;
+          float c[32];
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
             // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
@@ -505,7 +633,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* g0 = Gbuf + l * LDG;
             const float* wv = Wsh + ch * 32;
             const float* tv = Tsh + ch * 32;
-            float c[32];
 #pragma unroll
             for (int x = 0; x < 32; ++x) c[x] = g0[x];
             for (int m = 1; m < L; ++m) {
@@ -514,27 +641,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int x = 0; x < 32; ++x) c[x] += gm[x];
             }
             const float lthr = list.threshold();
-            uint32_t cand = 0;
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
-              const float dv = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);
-              cand |= (dv < lthr && dv <= thr_row ? 1u : 0u) << x;
-              ccand |= (dv <= tv[x] ? 1u : 0u) << x;
+              c[x] = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);  // D(t, j0 + x)
+              cand |= (c[x] < lthr && c[x] <= thr_row ? 1u : 0u) << x;
+              ccand |= (c[x] <= tv[x] ? 1u : 0u) << x;
             }
             cand &= valid;
             ccand &= valid & colrange;
-            // recompute (identically) the few pairs that enter the row's list
-            while (cand) {
-              const int x = __ffs(cand) - 1;
-              cand &= cand - 1;
-              float cc = g0[x];
-              for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + x];
-              const float dv = fmaxf(fmaf(-2.0f, cc, Wt + wv[x]), 0.0f);
-              if (dv < list.threshold() && dv <= thr_row) {
-                list.insert(dv, j0 + x);
-                ++cnt[0];
-              }
-            }
           }
           // column-side candidates, transposed by ballots: lane x of warp quadrant q
           // holds the rows q*32 + b of column x that pass the column's bound
@@ -549,58 +663,111 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           Cmask[q * 32 + lane] = cm;
           ptx::named_bar_sync(bar, kEpiThreads);
+          // every window sum of the chunk is done: a row with candidates replaces the
+          // first 32 entries of its Gram row by its distances (the carried columns
+          // 32.. stay), so that candidates are read back instead of recomputed
+          if (cand | ccand) {
+            float* drow = Gbuf + l * LDG;
+#pragma unroll
+            for (int x = 0; x < 32; ++x) drow[x] = c[x];
+          }
+          if (colrange) ptx::named_bar_sync(bar, kEpiThreads);  // other rows read them
           lap(4);
-          if (colrange && lane < 8 && ((colrange >> cx) & 1u)) {
-            // the column's list over the strip's rows: rows arrive in increasing
-            // order, so a strict compare keeps the smaller row first at equal
-            // distance ((distance, index) order)
-            const int j = j0 + cx;
-            const float wj = Wsh[ch * 32 + cx];
-            int n = 0;
+          // row side: the few distances that enter the row's list
+          while (cand) {
+            const int x = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const float dv = Gbuf[l * LDG + x];
+            if (dv < list.threshold() && dv <= thr_row) {
+              list.insert(dv, j0 + x);
+              ++cnt[0];
+            }
+          }
+          // column side, written by the rows themselves: column x's list holds its
+          // candidate rows in row order (slot = number of candidate rows before
+          // this one), unless more than k rows qualify, in which case the column's
+          // own thread below keeps the k best
+          while (ccand) {
+            const int x = __ffs(ccand) - 1;
+            ccand &= ccand - 1;
+            int before = __popc(Cmask[q * 32 + x] & ((1u << lane) - 1u)), ne = 0;
+#pragma unroll
             for (int wq = 0; wq < 4; ++wq) {
-              uint32_t mk = Cmask[wq * 32 + cx];
-              while (mk) {
-                const int r = wq * 32 + __ffs(mk) - 1;
-                mk &= mk - 1;
-                const float* g0 = Gbuf + r * LDG;
-                float cc = g0[cx];
-                for (int m = 1; m < L; ++m) cc += g0[m * (LDG + 1) + cx];
-                const float dv = fmaxf(fmaf(-2.0f, cc, Wrow[r] + wj), 0.0f);
-                int pos;
-                if (n < us.k) {
-                  pos = n++;
-                } else if (dv < Cld[(us.k - 1) * 32 + cx]) {
-                  pos = us.k - 1;
-                } else {
-                  continue;
-                }
-                while (pos > 0 && Cld[(pos - 1) * 32 + cx] > dv) {
-                  Cld[pos * 32 + cx] = Cld[(pos - 1) * 32 + cx];
-                  Cli[pos * 32 + cx] = Cli[(pos - 1) * 32 + cx];
-                  --pos;
-                }
-                Cld[pos * 32 + cx] = dv;
-                Cli[pos * 32 + cx] = us.T0 + r;
-              }
+              const int cq = __popc(Cmask[wq * 32 + x]);
+              ne += cq;
+              before += wq < q ? cq : 0;
             }
+            if (ne <= us.k) {
+              const long long li = cbase + (j0 + x - jsym);
+              w.col_d[li * w.kstride + before] = Gbuf[l * LDG + x];
+              w.col_i[li * w.kstride + before] = us.T0 + l;
+            }
+          }
+          if (colrange && lane < 8 && ((colrange >> cx) & 1u)) {
+            const int j = j0 + cx;
             const long long li = cbase + (j - jsym);
-            for (int pp = 0; pp < n; ++pp) {
-              w.col_d[li * w.kstride + pp] = Cld[pp * 32 + cx];
-              w.col_i[li * w.kstride + pp] = Cli[pp * 32 + cx];
+            int ne = 0;
+#pragma unroll
+            for (int wq = 0; wq < 4; ++wq) ne += __popc(Cmask[wq * 32 + cx]);
+            if (ne == us.k) {
+              // exactly k candidates: the largest is the k-th distance
+              float mx = 0.f;
+              for (int wq = 0; wq < 4; ++wq) {
+                uint32_t mk = Cmask[wq * 32 + cx];
+                while (mk) {
+                  const int r = wq * 32 + __ffs(mk) - 1;
+                  mk &= mk - 1;
+                  mx = fmaxf(mx, Gbuf[r * LDG + cx]);
+                }
+              }
+              publish_bound(w.thr + us.out_base + j, mx);
+            } else if (ne > us.k) {
+              // more than k: keep the k best in (distance, row) order; rows arrive in
+              // increasing order, so a strict compare keeps the smaller row first
+              int n = 0;
+              for (int wq = 0; wq < 4; ++wq) {
+                uint32_t mk = Cmask[wq * 32 + cx];
+                while (mk) {
+                  const int r = wq * 32 + __ffs(mk) - 1;
+                  mk &= mk - 1;
+                  const float dv = Gbuf[r * LDG + cx];
+                  int pos;
+                  if (n < us.k) {
+                    pos = n++;
+                  } else if (dv < Cld[(us.k - 1) * 32 + cx]) {
+                    pos = us.k - 1;
+                  } else {
+                    continue;
+                  }
+                  while (pos > 0 && Cld[(pos - 1) * 32 + cx] > dv) {
+                    Cld[pos * 32 + cx] = Cld[(pos - 1) * 32 + cx];
+                    Cli[pos * 32 + cx] = Cli[(pos - 1) * 32 + cx];
+                    --pos;
+                  }
+                  Cld[pos * 32 + cx] = dv;
+                  Cli[pos * 32 + cx] = us.T0 + r;
+                }
+              }
+              for (int pp = 0; pp < us.k; ++pp) {
+                w.col_d[li * w.kstride + pp] = Cld[pp * 32 + cx];
+                w.col_i[li * w.kstride + pp] = Cli[pp * 32 + cx];
+              }
+              publish_bound(w.thr + us.out_base + j, Cld[(us.k - 1) * 32 + cx]);
             }
-            w.col_n[li] = n;
-            cnt[3] += n > 0;
-            if (n == us.k) atomicMin(w.thr + us.out_base + j, __float_as_uint(Cld[(n - 1) * 32 + cx]));
+            w.col_n[li] = min(ne, us.k);
+            cnt[3] += ne > 0;
           }
           // the column side read other rows' Gram values: keep them until it is done
           if (colrange) ptx::named_bar_sync(bar, kEpiThreads);
           cnt[4] += et == 0;
           lap(5);
+          fold(false, gt + 1);  // the next tile's finished segments, if any
+          lap(2);
           ++gch;
         }
         if (row_ok) {
           const float kth = kth_of(list, us.k);
-          if (kth < thr_row) atomicMin(w.thr + us.out_base + t, __float_as_uint(kth));
+          if (kth < thr_row) publish_bound(w.thr + us.out_base + t, kth);
         }
       }
       if (!ok) break;
@@ -627,6 +794,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       lap(6);
       for (int i = 0; i < 6; ++i) atomicAdd(w.stats + kStatEpiWaitAcc + i, (unsigned long long)ph[i]);
       atomicAdd(w.stats + kStatEpiCycles, (unsigned long long)(clock64() - e_start));
+      atomicAdd(w.stats + kStatReserved, (unsigned long long)fold_cycles);
     }
   }
 
@@ -721,6 +889,8 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Tc
   p.stage_bytes = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
   p.nstages = pick_stages(split, a.kmax, a.Lmax);
   if (p.nstages < 2) return cudaErrorInvalidValue;
+  if (a.seg_k < KC || a.seg_k % KC != 0) return cudaErrorInvalidValue;
+  p.seg_kb = a.seg_k / KC;
   const size_t smem = fused_tc_smem_bytes(split, a.kmax, a.Lmax);
   const int k = a.kmax;
   if (k <= 4) return launch_k<4>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);

@@ -178,77 +178,89 @@ __global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
   mu[(size_t)b * D + p] = acc / (float)st.s[b].N;
 }
 
-// One warp per stacked day: x - mu(series) = hi + lo (two BF16 copies, pitch Dp) and
-// the FP64 norm of the centred row; FP32 squares summed 8 at a time before joining
-// the FP64 accumulator. VEC = 2 reads pairs (even D, 8-byte aligned rows).
-template <int VEC>
+// One warp per stacked day: the centred row x - mu(series) as two BF16 copies hi + lo
+// (split form; the BF16 form uses hi alone) in the tensor-core operand layout, its
+// FP64 norm, and its correction value.
+//
+// Layout: `groups` = ceil(D / 63) groups of 64 K entries. Group b holds the grid
+// points b, b + groups, b + 2 groups, ... (63 at most), so that every group samples
+// the whole grid and carries about 1/groups of the row's energy; entry 63 of every
+// group holds c = bf16(sqrt(n / groups)) in hi and -c in lo. The three split
+// products of that entry add hi_a hi_b + hi_a lo_b + lo_a hi_b = -c_a c_b to the
+// Gram accumulator once per group, so the tensor cores accumulate
+// G_ab - groups c_a c_b, which stays near zero for the close pairs that decide the
+// neighbour sets, instead of G_ab itself; the epilogue adds groups c_a c_b back in
+// FP32. A permutation of the grid points (the same for every row) leaves the Gram
+// unchanged. With kCorr false (BF16 form) the correction entries and c are zero.
+template <bool kCorr>
 __global__ void __launch_bounds__(256)
-    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int Dp,
+    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int groups,
                              const float* __restrict__ mu, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo, double* __restrict__ norms) {
+                             __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
+                             float* __restrict__ cval) {
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   const int b = find_series(st.s, st.n, r, false);
   const SeriesInfo& si = st.s[b];
   const int a = r - si.row_base;
+  const int Dp = groups * 64;
+  __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(hi + (size_t)r * Dp);
+  __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(lo + (size_t)r * Dp);
+  if (a >= si.N) {  // padding row between series: zeros
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.f, 0.f);
+    for (int q = lane; q < Dp / 2; q += 32) {
+      h2[q] = z;
+      l2[q] = z;
+    }
+    if (lane == 0) {
+      norms[r] = 0.0;
+      cval[r] = 0.f;
+    }
+    return;
+  }
   const float* x = si.X + (size_t)a * D;
   const float* m = mu + (size_t)b * D;
-  __nv_bfloat16* h = hi + (size_t)r * Dp;
-  __nv_bfloat16* lw = lo + (size_t)r * Dp;
+  // FP64 norm of the centred row: FP32 squares summed 8 at a time per lane
   double acc = 0.0;
   float part = 0.f;
   int cnt = 0;
-  if (a >= si.N) {  // padding row between series: zeros
-    for (int q = lane; q < Dp; q += 32) {
-      h[q] = __float2bfloat16_rn(0.f);
-      lw[q] = __float2bfloat16_rn(0.f);
-    }
-    if (lane == 0) norms[r] = 0.0;
-    return;
-  }
-  if (VEC == 2) {
-    const float2* x2 = reinterpret_cast<const float2*>(x);
-    const float2* m2 = reinterpret_cast<const float2*>(m);
-    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(h);
-    __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(lw);
-    for (int q = lane; q < Dp / 2; q += 32) {
-      float2 v = make_float2(0.f, 0.f);
-      if (q < D / 2) {
-        const float2 xv = x2[q];
-        const float2 mv = m2[q];
-        v = make_float2(xv.x - mv.x, xv.y - mv.y);
-      }
-      const __nv_bfloat162 hv = __floats2bfloat162_rn(v.x, v.y);
-      const float2 hf = __bfloat1622float2(hv);
-      h2[q] = hv;
-      l2[q] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-      part = fmaf(v.x, v.x, part);
-      part = fmaf(v.y, v.y, part);
-      if (++cnt == 4) {
-        acc += (double)part;
-        part = 0.f;
-        cnt = 0;
-      }
-    }
-  } else {
-    for (int q = lane; q < Dp; q += 32) {
-      const float v = q < D ? x[q] - m[q] : 0.f;
-      const __nv_bfloat16 hv = __float2bfloat16_rn(v);
-      h[q] = hv;
-      lw[q] = __float2bfloat16_rn(v - __bfloat162float(hv));
-      part = fmaf(v, v, part);
-      if (++cnt == 8) {
-        acc += (double)part;
-        part = 0.f;
-        cnt = 0;
-      }
+  for (int q = lane; q < D; q += 32) {
+    const float v = x[q] - m[q];
+    part = fmaf(v, v, part);
+    if (++cnt == 8) {
+      acc += (double)part;
+      part = 0.f;
+      cnt = 0;
     }
   }
   acc += (double)part;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) norms[r] = acc;
+  const float c = kCorr ? __bfloat162float(__float2bfloat16_rn((float)sqrt(acc / groups))) : 0.f;
+  // operand entries in pairs (2q, 2q + 1) of the permuted, grouped layout
+  for (int q = lane; q < Dp / 2; q += 32) {
+    const int g = (2 * q) >> 6, pos = (2 * q) & 63;
+    const int i0 = pos * groups + g, i1 = (pos + 1) * groups + g;
+    const float v0 = i0 < D ? __ldg(x + i0) - __ldg(m + i0) : 0.f;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
+    const __nv_bfloat16 lo0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+    __nv_bfloat16 h1, lo1;
+    if (pos + 1 == 63) {  // correction entry
+      h1 = __float2bfloat16_rn(c);
+      lo1 = __float2bfloat16_rn(-c);
+    } else {
+      const float v1 = i1 < D ? __ldg(x + i1) - __ldg(m + i1) : 0.f;
+      h1 = __float2bfloat16_rn(v1);
+      lo1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+    }
+    h2[q] = __halves2bfloat162(h0, h1);
+    l2[q] = __halves2bfloat162(lo0, lo1);
+  }
+  if (lane == 0) {
+    norms[r] = acc;
+    cval[r] = c;
+  }
 }
 
 // W of every stacked trajectory row: an explicit L-term FP64 sum of its series' norms.
@@ -410,10 +422,9 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       for (int s2 = lane; s2 < strip; s2 += 32) {
         const long long li = collist(s2);
         const int nn = w.col_n[li];
-        for (int p = 0; p < nn; ++p) {
+        for (int p = 0; p < nn; ++p) {  // column lists are not sorted
           const float d = w.col_d[li * ks + p];
-          if (d > thr) break;
-          push(d, w.col_i[li * ks + p]);
+          if (d <= thr) push(d, w.col_i[li * ks + p]);
         }
       }
     }
@@ -456,8 +467,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
           const long long li = collist(s2);
           const int nn = w.col_n[li];
           for (int p = 0; p < nn; ++p) {
-            if (w.col_d[li * ks + p] > thr) break;
-            consider(w.col_d[li * ks + p], w.col_i[li * ks + p]);
+            if (w.col_d[li * ks + p] <= thr) consider(w.col_d[li * ks + p], w.col_i[li * ks + p]);
           }
         }
       }
@@ -502,18 +512,18 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int Dp,
-                                     bool even_aligned, const float* mu, void* hi, void* lo,
-                                     double* norms, cudaStream_t st) {
+cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int groups,
+                                     bool correct, const float* mu, void* hi, void* lo,
+                                     double* norms, float* cval, cudaStream_t st) {
   const int blocks = (rows + 7) / 8;
-  if (even_aligned)
-    prep_split_series_kernel<2><<<blocks, 256, 0, st>>>(sr, rows, D, Dp, mu,
-                                                        static_cast<__nv_bfloat16*>(hi),
-                                                        static_cast<__nv_bfloat16*>(lo), norms);
+  if (correct)
+    prep_split_series_kernel<true><<<blocks, 256, 0, st>>>(
+        sr, rows, D, groups, mu, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo),
+        norms, cval);
   else
-    prep_split_series_kernel<1><<<blocks, 256, 0, st>>>(sr, rows, D, Dp, mu,
-                                                        static_cast<__nv_bfloat16*>(hi),
-                                                        static_cast<__nv_bfloat16*>(lo), norms);
+    prep_split_series_kernel<false><<<blocks, 256, 0, st>>>(
+        sr, rows, D, groups, mu, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo),
+        norms, cval);
   return cudaGetLastError();
 }
 

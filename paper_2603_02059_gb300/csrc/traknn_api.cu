@@ -76,6 +76,7 @@ struct traknn_ctx {
   int sym = 1;
   int unit_cols = 0;
   int autotune = 0;
+  int seg_k = kSegmentK;
   int stats = 0;
   unsigned long long* stats_dev = nullptr;
   TcPlan plan;
@@ -177,7 +178,7 @@ Layout make_layout(int64_t N, int64_t D, const Schedule& s) {
 static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 
 // Tensor-core work list of a batch. For each series: strips of 128 - (L-1) output
-// rows; units of `tiles` Gram tiles (each yielding 256 - (L-1) output columns);
+// rows; units of `tiles` Gram tiles (each yielding kTileCols - (L-1) output columns);
 // with the symmetric split only columns from each strip's own block on. Units
 // are ordered per series in groups of strips that run side by side (sharing A and
 // B tiles in L2), the groups from the last strip upwards. The band units (two
@@ -198,7 +199,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     const int M = N - L + 1;
     const int R = kTileRows - (L - 1);
     const int strips = (M + R - 1) / R;
-    const int cols = cols_opt > 0 ? cols_opt : tiles * (256 - (L - 1));
+    const int cols = cols_opt > 0 ? cols_opt : tiles * (kTileCols - (L - 1));
     const int slots = (M + cols - 1) / cols;
     SeriesInfo& si = p.table.s[b];
     si.N = N;
@@ -233,7 +234,8 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
           if (jlo < jhi) p.units.push_back(WorkUnit{b, s, jlo, jhi, c, {0, 0, 0}});
         }
     }
-    const int bw = std::max(0, (2 * 256 - (L - 1) - R) / 2);
+    // band: two tiles of columns centred on the strip's rows
+    const int bw = std::max(0, (2 * kTileCols - (L - 1) - R) / 2);
     for (int s = 0; s < strips; ++s) {
       const int T0 = s * R;
       const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
@@ -263,7 +265,8 @@ traknn_status check_handle(traknn_handle h) {
 }
 
 std::vector<int64_t> shape_key(const HostSeries* sd, int B, int64_t D, const traknn_ctx* h) {
-  std::vector<int64_t> key = {D, h->sym, h->unit_cols, (int64_t)h->precision, h->center, B};
+  std::vector<int64_t> key = {D, h->sym, h->unit_cols, (int64_t)h->precision, h->center, B,
+                              h->seg_k};
   for (int b = 0; b < B; ++b) {
     key.push_back(sd[b].N);
     key.push_back(sd[b].L);
@@ -278,6 +281,7 @@ struct TcBuffers {
   float* partial;
   float* mu;
   double* norms;
+  float* cval;
   float* W;
   void* hi;
   void* lo;
@@ -288,11 +292,12 @@ struct TcBuffers {
   float* col_d;
   int32_t* col_i;
   int* counter;
+  float* scratch;
   int Dp;
   size_t total;
 };
 
-TcBuffers tc_layout(const TcPlan& p, int64_t D, char* base) {
+TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
   TcBuffers b;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -301,12 +306,13 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, char* base) {
     off += bytes;
     return base + o;
   };
-  b.Dp = (int)align_up((size_t)D, 32);
+  b.Dp = tc_groups((int)D) * 64;
   const int B = p.table.n;
   const size_t ks = (size_t)p.kmax;
   b.partial = reinterpret_cast<float*>(take((size_t)B * kMeanSlices * D * sizeof(float)));
   b.mu = reinterpret_cast<float*>(take((size_t)B * D * sizeof(float)));
   b.norms = reinterpret_cast<double*>(take((size_t)p.rows * sizeof(double)));
+  b.cval = reinterpret_cast<float*>(take((size_t)p.rows * sizeof(float)));
   b.W = reinterpret_cast<float*>(take((size_t)p.out_rows * sizeof(float)));
   b.hi = take((size_t)p.rows * b.Dp * 2);
   b.lo = take((size_t)p.rows * b.Dp * 2);
@@ -317,6 +323,7 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, char* base) {
   b.col_d = reinterpret_cast<float*>(take((size_t)p.col_lists * ks * sizeof(float)));
   b.col_i = reinterpret_cast<int32_t*>(take((size_t)p.col_lists * ks * sizeof(int32_t)));
   b.counter = reinterpret_cast<int*>(take(256));
+  b.scratch = reinterpret_cast<float*>(take(tc_scratch_bytes(num_ctas)));
   b.total = off;
   return b;
 }
@@ -351,14 +358,14 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
     p.table.s[b].dist = sd[b].dist;
     p.table.s[b].score = sd[b].score;
   }
-  const TcBuffers probe = tc_layout(p, D, nullptr);
+  const TcBuffers probe = tc_layout(p, D, h->sm_count, nullptr);
   TRY_ST(ensure_buffer(h, &h->tcws, &h->tcws_bytes, probe.total));
-  *out = tc_layout(p, D, static_cast<char*>(h->tcws));
+  *out = tc_layout(p, D, h->sm_count, static_cast<char*>(h->tcws));
   return TRAKNN_OK;
 }
 
 // The launch sequence of one tensor-core call (also what a graph captures).
-traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D, bool even_aligned,
+traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
                          cudaStream_t s, bool record_events) {
   const TcPlan& p = h->plan;
   const SeriesTable& sr = p.table;
@@ -378,6 +385,10 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D, bool even
   a.err = h->err;
   a.wait_limit_ns = (long long)h->wait_limit_ms * 1000000LL;
   a.debug_withhold = h->debug_withhold;
+  a.seg_k = h->seg_k;
+  a.scratch = b.scratch;
+  a.groups = b.Dp / 64;
+  a.cval = b.cval;
 
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
@@ -396,8 +407,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D, bool even
 
   const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
   TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
-  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, b.Dp, even_aligned, b.mu, b.hi, b.lo,
-                                    b.norms, s));
+  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, b.Dp / 64, split, b.mu, b.hi, b.lo,
+                                    b.norms, b.cval, s));
   TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s));
   TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
   TRY_CUDA(cudaMemsetAsync(b.counter, 0, 2 * sizeof(int), s));
@@ -424,12 +435,6 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D, bool even
   return TRAKNN_OK;
 }
 
-bool inputs_even_aligned(const HostSeries* sd, int B, int64_t D) {
-  if (D % 2) return false;
-  for (int b = 0; b < B; ++b)
-    if (reinterpret_cast<uintptr_t>(sd[b].X) % 8) return false;
-  return true;
-}
 
 traknn_status validate_series(const HostSeries* sd, int B, int64_t D) {
   if (B < 1) return TRAKNN_ERR_INVALID_ARG;
@@ -456,7 +461,6 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
       *tiles = t.second;
       return TRAKNN_OK;
     }
-  const bool even = inputs_even_aligned(sd, B, D);
   cudaEvent_t e0, e1;
   TRY_CUDA(cudaEventCreate(&e0));
   TRY_CUDA(cudaEventCreate(&e1));
@@ -465,9 +469,9 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   for (int cand : {8, 16, 32}) {
     TcBuffers buf;
     TRY_ST(prepare_tc(h, sd, B, D, cand, s, &buf));
-    TRY_ST(enqueue_tc(h, buf, D, even, s, false));  // warm-up
+    TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
     TRY_CUDA(cudaEventRecord(e0, s));
-    TRY_ST(enqueue_tc(h, buf, D, even, s, false));
+    TRY_ST(enqueue_tc(h, buf, D, s, false));
     TRY_CUDA(cudaEventRecord(e1, s));
     TRY_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -493,8 +497,7 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
   TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
   TcBuffers buf;
   TRY_ST(prepare_tc(h, sd, B, D, tiles, s, &buf));
-  const bool even = inputs_even_aligned(sd, B, D);
-  if (!graph) return enqueue_tc(h, buf, D, even, s, h->profile != 0);
+  if (!graph) return enqueue_tc(h, buf, D, s, h->profile != 0);
 
   std::vector<int64_t> key = h->plan.key;
   for (int b = 0; b < B; ++b) {
@@ -514,11 +517,11 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
     }
   if (!h->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   // run once outside the capture (kernel attributes, first-use costs), then capture
-  TRY_ST(enqueue_tc(h, buf, D, even, s, false));
+  TRY_ST(enqueue_tc(h, buf, D, s, false));
   TRY_CUDA(cudaStreamSynchronize(s));
   const int64_t l0 = h->launches;
   TRY_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  const traknn_status st = enqueue_tc(h, buf, D, even, h->cap_stream, false);
+  const traknn_status st = enqueue_tc(h, buf, D, h->cap_stream, false);
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
   if (st != TRAKNN_OK) {
@@ -644,6 +647,10 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
       return TRAKNN_OK;
     case TRAKNN_OPT_AUTOTUNE:
       h->autotune = v ? 1 : 0;
+      return TRAKNN_OK;
+    case TRAKNN_OPT_SEGMENT_K:
+      if (v != 0 && (v < 32 || v % 32 != 0 || v > (1 << 20))) return TRAKNN_ERR_INVALID_ARG;
+      h->seg_k = v ? (int)v : kSegmentK;
       return TRAKNN_OK;
     case TRAKNN_OPT_STATS:
       if (v && !h->stats_dev) {

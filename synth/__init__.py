@@ -82,30 +82,56 @@ def _ar1_coeffs(rng, n_days, n_modes, phi):
 def make_slp_like(n_days: int, h: int, w: int, seed: int, *, n_modes: int = 40,
                   kmax: int = 4, phi: float = 0.8, std_hpa: float = 10.0,
                   annual_amp: float = 0.0, n_planted: int = 0,
-                  planted_len: int = 5, planted_sigma: float = 4.0):
-    """Return (X, meta): X is float32 of shape (n_days, h*w), row = day."""
+                  planted_len: int = 5, planted_sigma: float = 4.0,
+                  block_cols: int = 8192):
+    """Return (X, meta): X is float32 of shape (n_days, h*w), row = day.
+
+    The field is built in blocks of ``block_cols`` grid points (FP64 inside a
+    block), so that large grids need little more host memory than the output."""
     rng = np.random.default_rng(seed)
     cos_b, sin_b = _mode_basis(rng, h, w, n_modes, kmax)
     c = _ar1_coeffs(rng, n_days, n_modes, phi)
     basis = np.concatenate([cos_b, sin_b], axis=0)          # (2 n_modes, D)
     coef = np.concatenate([c.real, c.imag], axis=1)         # (n_days, 2 n_modes)
-    X = coef @ basis
-    X -= X.mean()
-    X *= std_hpa / X.std()
+    D = h * w
+    blocks = [(b, min(D, b + block_cols)) for b in range(0, D, block_cols)]
 
+    # global mean and standard deviation of the raw mode sum (two-pass per block)
+    total, count = 0.0, 0
+    for b0, b1 in blocks:
+        total += float((coef @ basis[:, b0:b1]).sum())
+        count += n_days * (b1 - b0)
+    mean = total / count
+    sq = 0.0
+    for b0, b1 in blocks:
+        sq += float(((coef @ basis[:, b0:b1] - mean) ** 2).sum())
+    scale = std_hpa / np.sqrt(sq / count)
+
+    doy = np.arange(n_days) % 365
     if annual_amp > 0.0:
         yy, xx = np.meshgrid(np.linspace(0, 1, h), np.linspace(0, 1, w), indexing="ij")
-        phase_map = (2.0 * np.pi * (0.3 * xx + 0.2 * yy)).reshape(1, -1)
-        doy = (np.arange(n_days) % 365).reshape(-1, 1)
-        X += annual_amp * np.cos(2.0 * np.pi * doy / 365.0 - phase_map)
-        # remove the daily climatology (mean of each calendar day over the years)
-        clim = np.zeros((365, X.shape[1]))
-        cnt = np.zeros((365, 1))
-        np.add.at(clim, doy[:, 0], X)
-        np.add.at(cnt, doy[:, 0], 1.0)
-        X -= (clim / np.maximum(cnt, 1.0))[doy[:, 0]]
+        phase_map = (2.0 * np.pi * (0.3 * xx + 0.2 * yy)).reshape(-1)
+        ang = 2.0 * np.pi * doy / 365.0
+    X = np.empty((n_days, D), dtype=np.float32)
+    for b0, b1 in blocks:
+        blk = (coef @ basis[:, b0:b1] - mean) * scale
+        if annual_amp > 0.0:
+            # cos(a - p) = cos a cos p + sin a sin p
+            blk += annual_amp * (np.cos(ang)[:, None] * np.cos(phase_map[b0:b1])[None, :]
+                                 + np.sin(ang)[:, None] * np.sin(phase_map[b0:b1])[None, :])
+            # remove the daily climatology (mean of each calendar day over the years)
+            for d in range(min(365, n_days)):
+                blk[d::365] -= blk[d::365].mean(axis=0)
+        X[:, b0:b1] = blk
 
-    std = float(X.std())
+    # standard deviation of the final field, accumulated in FP64 per block
+    s1 = s2 = 0.0
+    for b0, b1 in blocks:
+        v = X[:, b0:b1].astype(np.float64)
+        s1 += float(v.sum())
+        s2 += float((v * v).sum())
+    n = float(n_days) * D
+    std = float(np.sqrt(max(s2 / n - (s1 / n) ** 2, 0.0)))
     starts = []
     if n_planted > 0:
         gap = 4 * planted_len
@@ -121,11 +147,11 @@ def make_slp_like(n_days: int, h: int, w: int, seed: int, *, n_modes: int = 40,
             pc, ps = _mode_basis(rng, h, w, 6, kmax)
             pat = pc.sum(axis=0) + ps.sum(axis=0)
             pat *= planted_sigma * std / np.sqrt(np.mean(pat ** 2))
-            X[s:s + planted_len] += pat[None, :]
+            X[s:s + planted_len] += pat[None, :].astype(np.float32)
 
     meta = SynthMeta(n_days=n_days, h=h, w=w, seed=seed, planted_starts=starts,
                      planted_len=planted_len, std=std)
-    return np.ascontiguousarray(X, dtype=np.float32), meta
+    return X, meta
 
 
 # The workloads: (days, grid h, grid w, L, k, exclusion, extra generator options).

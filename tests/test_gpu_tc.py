@@ -161,3 +161,20 @@ def test_constant_series_ties_go_to_smaller_indices(tk, prec):
         exp = [j for j in range(M) if abs(j - t) > e][:k]
         assert list(idx[t]) == exp, t
     assert np.all(dist == 0) and np.all(score == 0)
+
+
+@pytest.mark.parametrize("seg", [64, 1024])
+def test_segmented_accumulation(tk, seg):
+    """Gram entries accumulated on the tensor cores in segments of `seg` grid points,
+    the segments added in FP32: parity with the oracle, and agreement with the
+    default accumulation."""
+    h = tk.get_handle()
+    X, _ = make_slp_like(1500, 46, 81, seed=77)
+    try:
+        h.set_option("segment_k", seg)
+        idx, dist, score = _run(tk, X, 5, 10, 4)
+    finally:
+        h.set_option("segment_k", 0)
+    check_full(X, 5, 10, 4, idx, dist, score, TOL["split_bf16"])
+    ref = _run(tk, X, 5, 10, 4)
+    assert np.allclose(score, ref[2], rtol=1e-4, atol=0)
