@@ -78,14 +78,19 @@ typedef enum {
                                         (upper triangle, Sec. 3.3), 0 both triangles (default 1) */
   TRAKNN_OPT_UNIT_COLS = 7,          /* tensor-core paths: output columns per work unit, 0 = auto */
   TRAKNN_OPT_STATS = 8,              /* 1: count kernel events (read with traknn_stats_read) */
-  TRAKNN_OPT_AUTOTUNE = 9,           /* tensor-core paths: 1 times 8, 16 and 32 Gram tiles per work
+  TRAKNN_OPT_AUTOTUNE = 9,           /* tensor-core paths: 1 times 4, 8 and 16 Gram tiles per work
                                         unit on the first call of each shape and keeps the fastest
                                         (ignored while TRAKNN_OPT_UNIT_COLS is set; default 0) */
-  TRAKNN_OPT_SEGMENT_K = 10          /* tensor-core paths: the tensor cores accumulate at most this
+  TRAKNN_OPT_SEGMENT_K = 10,         /* tensor-core paths: the tensor cores accumulate at most this
                                         many grid points (a multiple of 32) of a Gram entry before
                                         the partial sum is added in FP32 to the entry's running
                                         total; shorter segments bound the error of the tensor-core
                                         accumulation over large D (0 = default 8192) */
+  TRAKNN_OPT_GROUP_STRIPS = 11,      /* tensor-core paths: row strips whose work units are handed
+                                        out side by side (sharing operand tiles in L2; 0 = 19) */
+  TRAKNN_OPT_L2_KEEP_A = 12          /* tensor-core paths: 1 loads a unit's row-strip operand with
+                                        an L2 evict-last policy (it is re-read for every tile of
+                                        the unit; default 0) */
 } traknn_option;
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */

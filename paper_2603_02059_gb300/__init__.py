@@ -25,7 +25,8 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_AL
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
           "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7, "stats": 8,
-          "autotune": 9, "segment_k": 10}
+          "autotune": 9, "segment_k": 10,
+          "group_strips": 11, "l2_keep_a": 12}
 
 
 class Series(ctypes.Structure):

@@ -145,6 +145,7 @@ struct TcArgs {
   int seg_k;           // elements of K per accumulation segment (multiple of 32)
   int groups;          // K groups of the operand layout (see tc_groups)
   const float* cval;   // [rows] correction value c of every stacked operand row
+  int l2_keep_a;       // 1: load the strip operand with an L2 evict-last policy
   float* scratch;      // [CTAs][2][128 x 256] running tile totals (more than one segment)
 };
 

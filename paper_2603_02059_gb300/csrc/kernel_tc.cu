@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::prefetch_tensormap(&tmA_lo);
         ptx::prefetch_tensormap(&tmB_lo);
       }
+      const uint64_t pol_a = ptx::l2_policy_evict_last();
       int stage = 0, qs = 0;
       uint32_t phase = 0, qphase = 0, issued = 0, issued_par = 0;
       bool ok = true, withheld = false;
@@ -313,9 +314,16 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t fb = full0 + 8u * stage;
               const uint32_t sb = ring + (uint32_t)stage * p.stage_bytes;
               ptx::mbar_arrive_expect_tx(fb, p.stage_bytes);
-              ptx::tma_load_2d(sb, &tmA_hi, fb, kb * KC, a0);
+              // the strip operand (A) is read again for every tile of the unit: keep it
+              // in L2 ahead of the column tiles when asked to
+              if (a.l2_keep_a) {
+                ptx::tma_load_2d_hint(sb, &tmA_hi, fb, kb * KC, a0, pol_a);
+                if (p.split) ptx::tma_load_2d_hint(sb + kTileA, &tmA_lo, fb, kb * KC, a0, pol_a);
+              } else {
+                ptx::tma_load_2d(sb, &tmA_hi, fb, kb * KC, a0);
+                if (p.split) ptx::tma_load_2d(sb + kTileA, &tmA_lo, fb, kb * KC, a0);
+              }
               if (p.split) {
-                ptx::tma_load_2d(sb + kTileA, &tmA_lo, fb, kb * KC, a0);
                 ptx::tma_load_2d(sb + 2 * kTileA, &tmB_hi, fb, kb * KC, c0);
                 ptx::tma_load_2d(sb + 2 * kTileA + kTileB, &tmB_lo, fb, kb * KC, c0);
               } else {

@@ -238,24 +238,40 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   const float c = kCorr ? __bfloat162float(__float2bfloat16_rn((float)sqrt(acc / groups))) : 0.f;
-  // operand entries in pairs (2q, 2q + 1) of the permuted, grouped layout
-  for (int q = lane; q < Dp / 2; q += 32) {
-    const int g = (2 * q) >> 6, pos = (2 * q) & 63;
-    const int i0 = pos * groups + g, i1 = (pos + 1) * groups + g;
-    const float v0 = i0 < D ? __ldg(x + i0) - __ldg(m + i0) : 0.f;
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
-    const __nv_bfloat16 lo0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-    __nv_bfloat16 h1, lo1;
-    if (pos + 1 == 63) {  // correction entry
-      h1 = __float2bfloat16_rn(c);
-      lo1 = __float2bfloat16_rn(-c);
-    } else {
-      const float v1 = i1 < D ? __ldg(x + i1) - __ldg(m + i1) : 0.f;
-      h1 = __float2bfloat16_rn(v1);
-      lo1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+  // Lane g0 + lane builds group g0 + lane: its entry pos is grid point pos * groups + g,
+  // so for each pos the warp reads 32 consecutive grid points (coalesced), and each
+  // lane then writes its group's 64 entries (128 bytes per copy) with 16-byte stores.
+  for (int g0 = 0; g0 < groups; g0 += 32) {
+    const int g = g0 + lane;
+    if (g >= groups) break;
+    uint32_t hv[32], lv[32];  // 64 BF16 entries per copy, in pairs
+#pragma unroll
+    for (int pp = 0; pp < 32; ++pp) {
+      const int i0 = (2 * pp) * groups + g, i1 = (2 * pp + 1) * groups + g;
+      const float v0 = i0 < D ? x[i0] - m[i0] : 0.f;
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
+      const __nv_bfloat16 q0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+      __nv_bfloat16 h1, q1;
+      if (pp == 31) {  // entry 63: the correction entry
+        h1 = __float2bfloat16_rn(c);
+        q1 = __float2bfloat16_rn(-c);
+      } else {
+        const float v1 = i1 < D ? x[i1] - m[i1] : 0.f;
+        h1 = __float2bfloat16_rn(v1);
+        q1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+      }
+      const __nv_bfloat162 hp = __halves2bfloat162(h0, h1);
+      const __nv_bfloat162 lp = __halves2bfloat162(q0, q1);
+      hv[pp] = *reinterpret_cast<const uint32_t*>(&hp);
+      lv[pp] = *reinterpret_cast<const uint32_t*>(&lp);
     }
-    h2[q] = __halves2bfloat162(h0, h1);
-    l2[q] = __halves2bfloat162(lo0, lo1);
+    uint4* hd = reinterpret_cast<uint4*>(h2 + (size_t)g * 32);
+    uint4* ld = reinterpret_cast<uint4*>(l2 + (size_t)g * 32);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      hd[v] = make_uint4(hv[4 * v], hv[4 * v + 1], hv[4 * v + 2], hv[4 * v + 3]);
+      ld[v] = make_uint4(lv[4 * v], lv[4 * v + 1], lv[4 * v + 2], lv[4 * v + 3]);
+    }
   }
   if (lane == 0) {
     norms[r] = acc;

@@ -77,6 +77,8 @@ struct traknn_ctx {
   int unit_cols = 0;
   int autotune = 0;
   int seg_k = kSegmentK;
+  int group_strips = 0;
+  int l2_keep_a = 0;
   int stats = 0;
   unsigned long long* stats_dev = nullptr;
   TcPlan plan;
@@ -184,7 +186,7 @@ static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 // B tiles in L2), the groups from the last strip upwards. The band units (two
 // tiles of columns centred on each strip's rows) seed the row bounds first.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
-                TcPlan& p) {
+                int group_opt, TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
@@ -221,7 +223,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
       if (sym && first_col < M) off += M - first_col;
       p.slot_lo.push_back(sym ? (s * R) / cols : 0);
     }
-    const int group = std::max(1, std::min(strips, 19));
+    const int group = std::max(1, std::min(strips, group_opt > 0 ? group_opt : 19));
     const int ngroups = (strips + group - 1) / group;
     for (int gi = 0; gi < ngroups; ++gi) {
       const int g = sym ? ngroups - 1 - gi : gi;
@@ -266,7 +268,7 @@ traknn_status check_handle(traknn_handle h) {
 
 std::vector<int64_t> shape_key(const HostSeries* sd, int B, int64_t D, const traknn_ctx* h) {
   std::vector<int64_t> key = {D, h->sym, h->unit_cols, (int64_t)h->precision, h->center, B,
-                              h->seg_k};
+                              h->seg_k, h->group_strips, h->l2_keep_a};
   for (int b = 0; b < B; ++b) {
     key.push_back(sd[b].N);
     key.push_back(sd[b].L);
@@ -336,7 +338,7 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   key.push_back(tiles);
   TcPlan& p = h->plan;
   if (p.key != key) {
-    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, p);
+    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, p);
     p.key = key;
     const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
     const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
@@ -389,6 +391,7 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   a.scratch = b.scratch;
   a.groups = b.Dp / 64;
   a.cval = b.cval;
+  a.l2_keep_a = h->l2_keep_a;
 
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
@@ -450,10 +453,10 @@ traknn_status validate_series(const HostSeries* sd, int B, int64_t D) {
 
 // Tiles per work unit for this batch shape: the autotuned value when tuning is on
 // (each candidate timed once after a warm-up launch, the fastest kept per shape),
-// else 16.
+// else 8.
 traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
                          int* tiles) {
-  *tiles = 16;
+  *tiles = 8;
   if (!h->autotune || h->unit_cols > 0) return TRAKNN_OK;
   const std::vector<int64_t> key = shape_key(sd, B, D, h);
   for (auto& t : h->tuned)
@@ -465,8 +468,8 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   TRY_CUDA(cudaEventCreate(&e0));
   TRY_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_t = 16;
-  for (int cand : {8, 16, 32}) {
+  int best_t = 8;
+  for (int cand : {4, 8, 16}) {
     TcBuffers buf;
     TRY_ST(prepare_tc(h, sd, B, D, cand, s, &buf));
     TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
@@ -493,7 +496,7 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
 traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
                      bool graph) {
   if (!tc_available()) return TRAKNN_ERR_UNSUPPORTED;
-  int tiles = 16;
+  int tiles = 8;
   TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
   TcBuffers buf;
   TRY_ST(prepare_tc(h, sd, B, D, tiles, s, &buf));
@@ -647,6 +650,13 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
       return TRAKNN_OK;
     case TRAKNN_OPT_AUTOTUNE:
       h->autotune = v ? 1 : 0;
+      return TRAKNN_OK;
+    case TRAKNN_OPT_L2_KEEP_A:
+      h->l2_keep_a = v ? 1 : 0;
+      return TRAKNN_OK;
+    case TRAKNN_OPT_GROUP_STRIPS:
+      if (v < 0 || v > 4096) return TRAKNN_ERR_INVALID_ARG;
+      h->group_strips = (int)v;
       return TRAKNN_OK;
     case TRAKNN_OPT_SEGMENT_K:
       if (v != 0 && (v < 32 || v % 32 != 0 || v > (1 << 20))) return TRAKNN_ERR_INVALID_ARG;
