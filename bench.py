@@ -130,27 +130,24 @@ def measured_peaks():
             "fallback"
 
 
-def kernel_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if it still matches the
-    kernel source (profiles/traffic.json holds bytes + the source digest)."""
+def kernel_traffic():
+    """DRAM bytes per step of the fused kernel (band + main launch) from the committed
+    ncu summary, if it was taken on the current kernel source (digest match)."""
     import hashlib
-    p = os.path.join(PROFILE_DIR, "traffic.json")
+    import re
+    p = os.path.join(PROFILE_DIR, "fused_tc_kernel__euro_75y_46x81__dram.md")
     try:
         with open(p) as f:
-            rec = json.load(f).get(kernel_key)
-    except (OSError, ValueError):
-        return None
-    if not rec:
-        return None
-    src = os.path.join(ROOT, "paper_2603_02059_gb300", "csrc", rec["source"])
-    try:
-        with open(src, "rb") as f:
+            txt = f.read()
+        with open(os.path.join(ROOT, "paper_2603_02059_gb300", "csrc", "kernel_tc.cu"), "rb") as f:
             digest = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
         return None
-    if digest != rec.get("digest"):
+    m_b = re.search(r"^traffic_bytes_per_step:\s*(\d+)", txt, re.M)
+    m_d = re.search(r"^source_digest:\s*([0-9a-f]+)", txt, re.M)
+    if not m_b or not m_d or m_d.group(1) != digest:
         return None
-    return float(rec["bytes_per_launch"]) * float(rec.get("scale", 1.0))
+    return float(m_b.group(1))
 
 
 # --------------------------------------------------------------- our arm
@@ -232,7 +229,7 @@ def run_ours(args, ws, rank, local):
     peak = float(peaks.get("bf16_tflops_sustained", 1720.6))
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": kernel_traffic("fused_tc_split"),
+                "traffic": kernel_traffic() if args.workload == WORKLOAD else None,
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "kernel": "fused Gram/window/top-k (split-BF16 tcgen05)",
                 "kernel_ms": statistics.mean(kms_split) if kms_split else None,
