@@ -180,8 +180,6 @@ cudaError_t launch_col_mean(const float* X, int N, int D, float* partial, float*
                             bool center, cudaStream_t st);
 cudaError_t launch_prep_fp32(const float* X, int N, int D, int Dp, const float* mu,
                              float* Xc, double* norms, cudaStream_t st);
-cudaError_t launch_prep_split(const float* X, int N, int D, int Dp, const float* mu,
-                              void* hi, void* lo, double* norms, cudaStream_t st);
 cudaError_t launch_window(const double* norms, int M, int L, float* W, cudaStream_t st);
 cudaError_t launch_fused_fp32(const float* Xc, const FusedArgs& a, int num_ctas,
                               cudaStream_t st);

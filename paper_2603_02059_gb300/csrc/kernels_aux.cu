@@ -72,73 +72,6 @@ __global__ void prep_fp32_kernel(const float* __restrict__ X, int D, int Dp,
   if (threadIdx.x == 0) norms[a] = s;
 }
 
-// One block per day: x - mu = hi + lo with hi = bf16(x - mu), lo = bf16(x - mu - hi),
-// written as two BF16 copies (row pitch Dp, zero padded). The norm is taken of
-// the centred FP32 value.
-__global__ void prep_split_kernel(const float* __restrict__ X, int D, int Dp,
-                                  const float* __restrict__ mu, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo, double* __restrict__ norms) {
-  __shared__ double red[32];
-  const int a = blockIdx.x;
-  const float* x = X + (size_t)a * D;
-  double acc = 0.0;
-  for (int p = threadIdx.x; p < Dp; p += blockDim.x) {
-    const float v = p < D ? x[p] - mu[p] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    hi[(size_t)a * Dp + p] = h;
-    lo[(size_t)a * Dp + p] = l;
-    acc = fma((double)v, (double)v, acc);
-  }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) norms[a] = s;
-}
-
-// One warp per day (8 days per block): the same split as prep_split_kernel with
-// 8-byte loads and packed bf16x2 stores. Squares are formed in FP32 and summed
-// eight at a time before joining an FP64 accumulator; the partial sums carry a
-// relative rounding error of a few 1e-8, far below what the distances need.
-// Requires even D (rows of X 8-byte aligned) and Dp a multiple of 32.
-__global__ void __launch_bounds__(256)
-    prep_split_rows_kernel(const float* __restrict__ X, int N, int D, int Dp,
-                           const float* __restrict__ mu, __nv_bfloat162* __restrict__ hi,
-                           __nv_bfloat162* __restrict__ lo, double* __restrict__ norms) {
-  const int a = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (a >= N) return;
-  const float2* x = reinterpret_cast<const float2*>(X + (size_t)a * D);
-  const float2* m2 = reinterpret_cast<const float2*>(mu);
-  __nv_bfloat162* h = hi + (size_t)a * (Dp / 2);
-  __nv_bfloat162* lw = lo + (size_t)a * (Dp / 2);
-  const int D2 = D / 2, Dp2 = Dp / 2;
-  double acc = 0.0;
-  float part = 0.f;
-  int cnt = 0;
-  for (int q = lane; q < Dp2; q += 32) {
-    float2 v = make_float2(0.f, 0.f);
-    if (q < D2) {
-      const float2 xv = x[q];
-      const float2 mv = m2[q];
-      v = make_float2(xv.x - mv.x, xv.y - mv.y);
-    }
-    const __nv_bfloat162 hv = __floats2bfloat162_rn(v.x, v.y);
-    const float2 hf = __bfloat1622float2(hv);
-    h[q] = hv;
-    lw[q] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-    part = fmaf(v.x, v.x, part);
-    part = fmaf(v.y, v.y, part);
-    if (++cnt == 4) {
-      acc += (double)part;
-      part = 0.f;
-      cnt = 0;
-    }
-  }
-  acc += (double)part;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) norms[a] = acc;
-}
-
 // Index of the series whose [base, base + count) range of stacked rows holds r.
 __device__ __forceinline__ int find_series(const SeriesInfo* sr, int ns, int r, bool traj) {
   int lo = 0, hi = ns - 1;
@@ -560,18 +493,6 @@ cudaError_t launch_col_mean(const float* X, int N, int D, float* partial, float*
 cudaError_t launch_prep_fp32(const float* X, int N, int D, int Dp, const float* mu, float* Xc,
                              double* norms, cudaStream_t st) {
   prep_fp32_kernel<<<N, 256, 0, st>>>(X, D, Dp, mu, Xc, norms);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_prep_split(const float* X, int N, int D, int Dp, const float* mu, void* hi,
-                              void* lo, double* norms, cudaStream_t st) {
-  const bool vec = (D % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 8 == 0);
-  if (vec)
-    prep_split_rows_kernel<<<(N + 7) / 8, 256, 0, st>>>(
-        X, N, D, Dp, mu, static_cast<__nv_bfloat162*>(hi), static_cast<__nv_bfloat162*>(lo), norms);
-  else
-    prep_split_kernel<<<N, 256, 0, st>>>(X, D, Dp, mu, static_cast<__nv_bfloat16*>(hi),
-                                         static_cast<__nv_bfloat16*>(lo), norms);
   return cudaGetLastError();
 }
 
