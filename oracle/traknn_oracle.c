@@ -27,6 +27,11 @@
  *   d/dX[a] = sum_t (2 g_t / k) sum_{j in N_t} sum_m (X[t+m] - X[j+m])
  *                                   * ([a == t+m] - [a == j+m]).
  *
+ * Optional grid-point weights w_p >= 0 (the *_w entry points; NULL = all ones)
+ * turn the snapshot distance into sum_p w_p (X[a,p] - X[b,p])^2, e.g. area
+ * weights proportional to the cosine of latitude (Sec. 5, composite analysis);
+ * the adjoint then carries the same factor w_p.
+ *
  * Parity pins: every function here is checked by tests against closed forms,
  * invariants and brute-force enumerations (see tests/test_oracle_pins.py).
  */
@@ -85,14 +90,14 @@ int oracle_num_threads(int nthreads) { return resolve_threads(nthreads); }
 
 /* ------------------------------------------------ Eq. 2, snapshot term */
 
-/* S(a,b) by direct differences of the two days' fields. */
-static double snapshot_sqdist(const float* X, int64_t D, int64_t a, int64_t b) {
+/* S(a,b) by direct differences of the two days' fields (weighted when w != NULL). */
+static double snapshot_sqdist(const float* X, int64_t D, const double* w, int64_t a, int64_t b) {
   const float* xa = X + a * D;
   const float* xb = X + b * D;
   double s = 0.0;
   for (int64_t p = 0; p < D; ++p) {
     double d = (double)xa[p] - (double)xb[p];
-    s += d * d;
+    s += w ? w[p] * (d * d) : d * d;
   }
   return s;
 }
@@ -100,6 +105,7 @@ static double snapshot_sqdist(const float* X, int64_t D, int64_t a, int64_t b) {
 typedef struct {
   const float* X;
   int64_t N, D;
+  const double* w;
   double* S;
 } smat_ctx;
 
@@ -107,18 +113,23 @@ static void smat_row(void* p, int64_t a) {
   smat_ctx* c = (smat_ctx*)p;
   c->S[a * c->N + a] = 0.0;
   for (int64_t b = a + 1; b < c->N; ++b) {
-    double s = snapshot_sqdist(c->X, c->D, a, b);
+    double s = snapshot_sqdist(c->X, c->D, c->w, a, b);
     c->S[a * c->N + b] = s;
     c->S[b * c->N + a] = s;
   }
 }
 
-/* Full N x N snapshot distance matrix (row-major). */
-int oracle_snapshot_matrix(const float* X, int64_t N, int64_t D, double* S, int nthreads) {
+/* Full N x N snapshot distance matrix (row-major); w: [D] weights or NULL. */
+int oracle_snapshot_matrix_w(const float* X, int64_t N, int64_t D, const double* w, double* S,
+                             int nthreads) {
   if (!X || !S || N < 1 || D < 1) return ORACLE_ERR_ARGS;
-  smat_ctx c = {X, N, D, S};
+  smat_ctx c = {X, N, D, w, S};
   parallel_rows(smat_row, &c, N, nthreads);
   return ORACLE_OK;
+}
+
+int oracle_snapshot_matrix(const float* X, int64_t N, int64_t D, double* S, int nthreads) {
+  return oracle_snapshot_matrix_w(X, N, D, NULL, S, nthreads);
 }
 
 /* ------------------------------------------------ Eq. 2, trajectory sum */
@@ -140,6 +151,7 @@ typedef struct {
   const float* X;
   int64_t N, D, M;
   int L;
+  const double* w;
   const int64_t* rows;
   double* out;
 } trows_ctx;
@@ -152,20 +164,25 @@ static void trows_row(void* p, int64_t r) {
   /* add the L snapshot terms of Eq. 2, one day offset m at a time */
   for (int m = 0; m < c->L; ++m)
     for (int64_t j = 0; j < c->M; ++j)
-      out[j] += snapshot_sqdist(c->X, c->D, t + m, j + m);
+      out[j] += snapshot_sqdist(c->X, c->D, c->w, t + m, j + m);
 }
 
 /* Rows of the trajectory distance matrix, computed from X directly: for each
  * requested t, out[r*M + j] = D(t, j) for every j in [0, M). */
-int oracle_traj_rows(const float* X, int64_t N, int64_t D, int L, const int64_t* rows,
-                     int64_t nrows, double* out, int nthreads) {
+int oracle_traj_rows_w(const float* X, int64_t N, int64_t D, int L, const double* w,
+                       const int64_t* rows, int64_t nrows, double* out, int nthreads) {
   if (!X || !rows || !out || L < 1 || L > N || D < 1) return ORACLE_ERR_ARGS;
   int64_t M = N - L + 1;
   for (int64_t r = 0; r < nrows; ++r)
     if (rows[r] < 0 || rows[r] >= M) return ORACLE_ERR_ARGS;
-  trows_ctx c = {X, N, D, M, L, rows, out};
+  trows_ctx c = {X, N, D, M, L, w, rows, out};
   parallel_rows(trows_row, &c, nrows, nthreads);
   return ORACLE_OK;
+}
+
+int oracle_traj_rows(const float* X, int64_t N, int64_t D, int L, const int64_t* rows,
+                     int64_t nrows, double* out, int nthreads) {
+  return oracle_traj_rows_w(X, N, D, L, NULL, rows, nrows, out, nthreads);
 }
 
 /* ------------------------------------------ kNN set and score (Eq. 3) */
@@ -220,8 +237,9 @@ int oracle_knn_from_rows(const double* Drows, const int64_t* rows, int64_t nrows
 }
 
 /* Whole pipeline for all M trajectories (small N only: it stores S and D). */
-int oracle_knn_scores(const float* X, int64_t N, int64_t D, int L, int k, int kk, int e,
-                      int32_t* idx, double* dist, double* score, double* Dt_out, int nthreads) {
+int oracle_knn_scores_w(const float* X, int64_t N, int64_t D, int L, const double* w, int k,
+                        int kk, int e, int32_t* idx, double* dist, double* score, double* Dt_out,
+                        int nthreads) {
   if (!X || L < 1 || L > N || k < 1 || kk < k || e < 0) return ORACLE_ERR_ARGS;
   int64_t M = N - L + 1;
   double* S = (double*)malloc(sizeof(double) * (size_t)(N * N));
@@ -231,7 +249,7 @@ int oracle_knn_scores(const float* X, int64_t N, int64_t D, int L, int k, int kk
     free(S); if (!Dt_out) free(Dt); free(rows);
     return ORACLE_ERR_NOMEM;
   }
-  int rc = oracle_snapshot_matrix(X, N, D, S, nthreads);
+  int rc = oracle_snapshot_matrix_w(X, N, D, w, S, nthreads);
   if (rc == ORACLE_OK) rc = oracle_traj_matrix(S, N, L, Dt);
   for (int64_t t = 0; t < M; ++t) rows[t] = t;
   if (rc == ORACLE_OK) rc = oracle_knn_from_rows(Dt, rows, M, M, k, kk, e, idx, dist, score);
@@ -240,12 +258,17 @@ int oracle_knn_scores(const float* X, int64_t N, int64_t D, int L, int k, int kk
   return rc;
 }
 
+int oracle_knn_scores(const float* X, int64_t N, int64_t D, int L, int k, int kk, int e,
+                      int32_t* idx, double* dist, double* score, double* Dt_out, int nthreads) {
+  return oracle_knn_scores_w(X, N, D, L, NULL, k, kk, e, idx, dist, score, Dt_out, nthreads);
+}
+
 /* ------------------------------------- adjoint with fixed neighbour sets */
 
 /* dX (N x D, overwritten) = d( sum_t g[t] s_t ) / dX, neighbour sets idx
  * (M x k) held fixed. Accumulated in FP64 exactly as the formula reads. */
-int oracle_score_grad(const float* X, int64_t N, int64_t D, int L, int k, const int32_t* idx,
-                      const double* g, double* dX) {
+int oracle_score_grad_w(const float* X, int64_t N, int64_t D, int L, const double* wgt, int k,
+                        const int32_t* idx, const double* g, double* dX) {
   if (!X || !idx || !g || !dX || L < 1 || L > N || k < 1) return ORACLE_ERR_ARGS;
   int64_t M = N - L + 1;
   memset(dX, 0, sizeof(double) * (size_t)(N * D));
@@ -261,6 +284,7 @@ int oracle_score_grad(const float* X, int64_t N, int64_t D, int L, int k, const 
         double* gb = dX + (j + m) * D;
         for (int64_t p = 0; p < D; ++p) {
           double diff = (double)xa[p] - (double)xb[p];
+          if (wgt) diff *= wgt[p];
           ga[p] += w * diff;
           gb[p] -= w * diff;
         }
@@ -268,4 +292,9 @@ int oracle_score_grad(const float* X, int64_t N, int64_t D, int L, int k, const 
     }
   }
   return ORACLE_OK;
+}
+
+int oracle_score_grad(const float* X, int64_t N, int64_t D, int L, int k, const int32_t* idx,
+                      const double* g, double* dX) {
+  return oracle_score_grad_w(X, N, D, L, NULL, k, idx, g, dX);
 }
