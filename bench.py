@@ -470,7 +470,57 @@ def suite_adjoint(args):
             "frac": gbs / peaks["hbm_gbs"], "peak_source": src}
 
 
-SUITES = {"precision": suite_precision, "batched": suite_batched, "adjoint": suite_adjoint}
+def suite_ext(args):
+    """75-year workload: the forward pass with cosine-of-latitude grid-point weights
+    against the unweighted one, and the statistics kernel (scores for every k' <= k and
+    the local intrinsic dimension) on its neighbour lists (HBM-bound: reads M k floats,
+    writes M k + M floats)."""
+    import torch
+
+    import paper_2603_02059_gb300 as tk
+    from synth import config_inputs
+    X, meta, cfg = config_inputs(WORKLOAD)
+    N, D = X.shape
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    M = N - L + 1
+    Xd = torch.from_numpy(X).cuda()
+    h = tk.get_handle()
+    out = (torch.empty((M, k), dtype=torch.int32, device="cuda"),
+           torch.empty((M, k), dtype=torch.float32, device="cuda"),
+           torch.empty((M,), dtype=torch.float32, device="cuda"))
+    ms_plain = _events_ms(lambda: tk.knn_scores(Xd, L, k, e, handle=h, out=out), args.steps, 3)
+    lat = np.deg2rad(np.linspace(72.0, 27.0, 46))
+    w = torch.from_numpy(np.repeat(np.cos(lat), 81).astype(np.float32)).cuda()
+    h.set_grid_weights(w)
+    ms_w = _events_ms(lambda: tk.knn_scores(Xd, L, k, e, handle=h, out=out), args.steps, 3)
+    h.set_grid_weights(None)
+    dist = out[1]
+    ms_stats = _events_ms(lambda: tk.knn_stats(dist, k_id=k, handle=h), 20, 3)
+    if h.sync_status() != 0:
+        raise RuntimeError("device-side failure")
+    peaks, src = measured_peaks()
+    nbytes = M * k * 4 * 2 + M * 4
+    gbs = nbytes / (ms_stats * 1e-3) / 1e9
+    # small-D form: 75 years of 32-value fields (a stand-in for PCA-reduced data)
+    from synth import make_slp_like
+    Xs, _ = make_slp_like(N, 4, 8, seed=20260310, annual_amp=5.0)
+    Xsd = torch.from_numpy(Xs).cuda()
+    small = {}
+    for prec in ("split_bf16", "fp32"):
+        ms = _events_ms(lambda: tk.knn_scores(Xsd, L, k, e, precision=prec, handle=h),
+                        args.steps if prec == "split_bf16" else 2, 2)
+        small[prec] = {"ms_per_step": ms, "pairs_per_s": float(M) * M / (ms * 1e-3)}
+    if h.sync_status() != 0:
+        raise RuntimeError("device-side failure")
+    return {"suite": "ext", "workload": f"{WORKLOAD}: N={N}, D={D}, L={L}, k={k}",
+            "forward_ms": ms_plain, "forward_weighted_ms": ms_w,
+            "stats_ms": ms_stats, "stats_bytes": nbytes, "stats_gbs": gbs,
+            "stats_frac_hbm": gbs / peaks["hbm_gbs"], "peak_source": src,
+            "small_D": {"workload": f"N={N}, D=32 (4x8), L={L}, k={k}", **small}}
+
+
+SUITES = {"precision": suite_precision, "batched": suite_batched, "adjoint": suite_adjoint,
+          "ext": suite_ext}
 
 
 # --------------------------------------------------------------- reference arm

@@ -168,6 +168,33 @@ typedef struct {
 traknn_status traknn_knn_scores_batched(traknn_handle handle, const traknn_series* series, int B,
                                         int64_t D, void* stream);
 
+/* Grid-point weights: with weights w (D values >= 0, DEVICE pointer, caller-owned,
+ * read by every later call on this handle until cleared) the snapshot distance of
+ * Eq. 2 becomes sum_p w_p (X[a,p] - X[b,p])^2 in every forward path of the handle
+ * (tensor-core and FP32) and in traknn_score_backward (dX carries the factor w_p).
+ * Area weights proportional to the cosine of latitude (Sec. 5, composite analysis)
+ * are the intended use. weights = NULL clears them. Calls whose D differs from
+ * the D given here return TRAKNN_ERR_INVALID_ARG. traknn_knn_scores_static ignores
+ * weights (it has no handle). */
+traknn_status traknn_set_grid_weights(traknn_handle handle, const float* weights, int64_t D);
+
+/* Statistics of sorted neighbour distance lists (DEVICE pointers, asynchronous):
+ *   nbr_dist      [M x k] float32, each row ascending (as traknn_knn_scores returns it)
+ *   prefix_scores [M x k] float32 out, or NULL: prefix_scores[t][k'-1] = the rarity
+ *                 score of Eq. 3 with k' neighbours, for every k' = 1..k (the neighbour
+ *                 set for k' is the first k' of the list for k: Sec. 6 notes that the
+ *                 top-k results of a larger k contain those of every smaller k);
+ *                 summed in FP64
+ *   local_id      [M] float32 out, or NULL: the local intrinsic dimension of every
+ *                 trajectory by the maximum-likelihood kNN estimator of Levina and
+ *                 Bickel with k_id neighbours (2 <= k_id <= k), as in the intrinsic
+ *                 dimension study of Sec. 4: [ (1/(k_id-1)) sum_{j<k_id} log(T_k_id/T_j) ]^-1
+ *                 with T_j = sqrt(nbr_dist[t][j-1]); NaN when one of the first k_id
+ *                 distances is zero or all of them are equal
+ * At least one output must be given. */
+traknn_status traknn_knn_stats(traknn_handle handle, const float* nbr_dist, int64_t M, int k,
+                               float* prefix_scores, int k_id, float* local_id, void* stream);
+
 /* Forward pass for callers that cannot allocate device memory. There is no
  * counterpart in the paper: this is an interface addition of this library.
  *

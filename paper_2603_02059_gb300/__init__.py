@@ -70,6 +70,8 @@ def lib():
                 "traknn_knn_scores_static": [P, I64, I64, I, I, I, P, P, P, P],
                 "traknn_stats_read": [P, P, I],
                 "traknn_knn_scores_batched": [P, P, I, I64, P],
+                "traknn_set_grid_weights": [P, P, I64],
+                "traknn_knn_stats": [P, P, I64, I, P, I, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -138,6 +140,20 @@ class Handle:
             self.set_option("unit_cols", int(unit_cols))
         if autotune is not None:
             self.set_option("autotune", int(autotune))
+
+    def set_grid_weights(self, w):
+        """Grid-point weights for later calls (a [D] float32 CUDA tensor kept alive by
+        the handle), or None to clear them."""
+        if w is None:
+            _check(lib().traknn_set_grid_weights(self._h, None, 0), "set_grid_weights")
+            self._weights = None
+            return
+        w = w.to(torch.float32).contiguous()
+        if not w.is_cuda or w.dim() != 1:
+            raise ValueError("weights must be a 1-D CUDA tensor")
+        _check(lib().traknn_set_grid_weights(self._h, w.data_ptr(), w.numel()),
+               "set_grid_weights")
+        self._weights = w
 
     def profile_read(self, max_n: int = 256):
         """Durations (ms) of the fused Gram/top-k kernel of recent profiled calls."""
@@ -250,6 +266,28 @@ def knn_scores_batched(series, *, precision: str = "split_bf16", center: bool = 
                                          D, ctypes.c_void_p(s.cuda_stream))
     _check(rc, "traknn_knn_scores_batched")
     return results
+
+
+def knn_stats(dist: torch.Tensor, k_id: int | None = None, *, prefix: bool = True,
+              handle: Handle | None = None):
+    """From sorted neighbour distances [M, k] (as knn_scores returns them): the scores
+    for every k' <= k ([M, k], column k'-1) and, if k_id is given, the local intrinsic
+    dimension of every row with k_id neighbours ([M]). Returns (prefix or None,
+    local_id or None)."""
+    if not dist.is_cuda or dist.dtype != torch.float32 or dist.dim() != 2:
+        raise ValueError("dist must be a 2-D float32 CUDA tensor")
+    dist = dist.contiguous()
+    M, k = dist.shape
+    h = handle or get_handle(dist.device.index)
+    pre = torch.empty((M, k), dtype=torch.float32, device=dist.device) if prefix else None
+    lid = torch.empty((M,), dtype=torch.float32, device=dist.device) if k_id else None
+    s = torch.cuda.current_stream(dist.device)
+    rc = lib().traknn_knn_stats(h._h, dist.data_ptr(), M, k,
+                                pre.data_ptr() if pre is not None else None, int(k_id or 0),
+                                lid.data_ptr() if lid is not None else None,
+                                ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_stats")
+    return pre, lid
 
 
 def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,

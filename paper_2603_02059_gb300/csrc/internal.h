@@ -178,8 +178,9 @@ enum : int {
 // ----------------------------------------------------------------- launchers
 cudaError_t launch_col_mean(const float* X, int N, int D, float* partial, float* mu,
                             bool center, cudaStream_t st);
+// wts: optional [D] grid-point weights (the values are scaled by sqrt(w_p)), or null.
 cudaError_t launch_prep_fp32(const float* X, int N, int D, int Dp, const float* mu,
-                             float* Xc, double* norms, cudaStream_t st);
+                             const float* wts, float* Xc, double* norms, cudaStream_t st);
 cudaError_t launch_window(const double* norms, int M, int L, float* W, cudaStream_t st);
 cudaError_t launch_fused_fp32(const float* Xc, const FusedArgs& a, int num_ctas,
                               cudaStream_t st);
@@ -198,8 +199,8 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
 // entries (63 permuted grid points + 1 correction entry); pitch groups * 64.
 inline int tc_groups(int D) { return (D + 62) / 63; }
 cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int groups,
-                                     bool correct, const float* mu, void* hi, void* lo,
-                                     double* norms, float* cval, cudaStream_t st);
+                                     bool correct, const float* mu, const float* wts, void* hi,
+                                     void* lo, double* norms, float* cval, cudaStream_t st);
 cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
                                  float* W, cudaStream_t st);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
@@ -207,9 +208,14 @@ cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* s
 // Adjoint of the summed weighted score (kernels_adjoint.cu); `ws` must hold
 // adjoint_workspace_bytes(M, k) bytes. Adds the number of launches to *launches.
 size_t adjoint_workspace_bytes(int M, int k);
+// wts: optional [D] grid-point weights (dX is multiplied by w_p), or null.
 cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int32_t* idx,
-                           const float* g, float* dX, void* ws, int* err, cudaStream_t st,
-                           int* launches);
+                           const float* g, const float* wts, float* dX, void* ws, int* err,
+                           cudaStream_t st, int* launches);
+// Scores for every k' <= k (prefix means of each sorted row, FP64 sums) and the
+// Levina-Bickel local intrinsic dimension for k_id <= k; either output may be null.
+cudaError_t launch_knn_stats(const float* dist, int M, int k, float* prefix, int k_id,
+                             float* local_id, cudaStream_t st);
 size_t fused_fp32_smem_bytes(int k);
 // False until the tensor-core kernel is compiled in.
 bool tc_available();

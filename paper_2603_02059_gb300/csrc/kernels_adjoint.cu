@@ -6,6 +6,8 @@
 // The incidences of day a are
 //   forward:  t in [a-L+1, a], j in N_t,             b = j + (a - t)
 //   reverse:  j in [a-L+1, a], t with j in N_t,       b = t + (a - j)
+// With grid-point weights w_p (distance sum_p w_p (x_p - y_p)^2) every term carries
+// the factor w_p, applied once to the finished sum.
 // Each output row is owned by one CTA that sums its incidences in a fixed order,
 // so no floating-point atomics are used and the result is bitwise reproducible.
 // The reverse lists (who has j as a neighbour) come from a counting sort whose
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kGatherThreads)
     adj_gather_kernel(const float* __restrict__ X, int N, int D, int L, int M, int k,
                       const int32_t* __restrict__ idx, const float* __restrict__ g,
                       const int* __restrict__ off, const int* __restrict__ rev,
-                      float* __restrict__ dX) {
+                      const float* __restrict__ wts, float* __restrict__ dX) {
   const int a = blockIdx.x;
   const float* xa = X + (size_t)a * D;
   const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kGatherThreads)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int p = p0 + u * kGatherThreads + threadIdx.x;
-      if (p < D) dX[(size_t)a * D + p] = acc[u];
+      if (p < D) dX[(size_t)a * D + p] = wts ? acc[u] * wts[p] : acc[u];
     }
   }
 }
@@ -153,8 +155,8 @@ size_t adjoint_workspace_bytes(int M, int k) {
 }
 
 cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int32_t* idx,
-                           const float* g, float* dX, void* ws, int* err, cudaStream_t st,
-                           int* launches) {
+                           const float* g, const float* wts, float* dX, void* ws, int* err,
+                           cudaStream_t st, int* launches) {
   const int M = N - L + 1;
   int* count = static_cast<int*>(ws);
   int* cursor = count + M;
@@ -168,7 +170,7 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_scan_kernel<<<1, 1024, 0, st>>>(count, M, off);
   adj_fill_kernel<<<blocks, 256, 0, st>>>(idx, M, k, off, cursor, rev);
   adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, M, rev);
-  adj_gather_kernel<<<N, kGatherThreads, 0, st>>>(X, N, D, L, M, k, idx, g, off, rev, dX);
+  adj_gather_kernel<<<N, kGatherThreads, 0, st>>>(X, N, D, L, M, k, idx, g, off, rev, wts, dX);
   *launches += 5;
   return cudaGetLastError();
 }

@@ -56,15 +56,16 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // One block per day: centred FP32 copy (row pitch Dp, zero padded) and the
 // FP64 squared norm of the centred row.
 __global__ void prep_fp32_kernel(const float* __restrict__ X, int D, int Dp,
-                                 const float* __restrict__ mu, float* __restrict__ Xc,
-                                 double* __restrict__ norms) {
+                                 const float* __restrict__ mu, const float* __restrict__ wts,
+                                 float* __restrict__ Xc, double* __restrict__ norms) {
   __shared__ double red[32];
   const int a = blockIdx.x;
   const float* x = X + (size_t)a * D;
   float* y = Xc + (size_t)a * Dp;
   double acc = 0.0;
   for (int p = threadIdx.x; p < Dp; p += blockDim.x) {
-    const float v = p < D ? x[p] - mu[p] : 0.f;
+    float v = p < D ? x[p] - mu[p] : 0.f;
+    if (wts && p < D) v *= sqrtf(wts[p]);  // grid-point weight w_p enters as sqrt(w_p)
     y[p] = v;
     acc = fma((double)v, (double)v, acc);
   }
@@ -128,9 +129,9 @@ __global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
 template <bool kCorr>
 __global__ void __launch_bounds__(256)
     prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int groups,
-                             const float* __restrict__ mu, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
-                             float* __restrict__ cval) {
+                             const float* __restrict__ mu, const float* __restrict__ wts,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                             double* __restrict__ norms, float* __restrict__ cval) {
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
@@ -158,8 +159,10 @@ __global__ void __launch_bounds__(256)
   double acc = 0.0;
   float part = 0.f;
   int cnt = 0;
+  // grid-point weights w_p enter the distance as sqrt(w_p) scalings of the values
+  auto val = [&](int i) { return wts ? (x[i] - m[i]) * sqrtf(wts[i]) : x[i] - m[i]; };
   for (int q = lane; q < D; q += 32) {
-    const float v = x[q] - m[q];
+    const float v = val(q);
     part = fmaf(v, v, part);
     if (++cnt == 8) {
       acc += (double)part;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int pp = 0; pp < 32; ++pp) {
       const int i0 = (2 * pp) * groups + g, i1 = (2 * pp + 1) * groups + g;
-      const float v0 = i0 < D ? x[i0] - m[i0] : 0.f;
+      const float v0 = i0 < D ? val(i0) : 0.f;
       const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
       const __nv_bfloat16 q0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
       __nv_bfloat16 h1, q1;
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(256)
         h1 = __float2bfloat16_rn(c);
         q1 = __float2bfloat16_rn(-c);
       } else {
-        const float v1 = i1 < D ? x[i1] - m[i1] : 0.f;
+        const float v1 = i1 < D ? val(i1) : 0.f;
         h1 = __float2bfloat16_rn(v1);
         q1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
       }
@@ -462,17 +465,17 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
 }
 
 cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int groups,
-                                     bool correct, const float* mu, void* hi, void* lo,
-                                     double* norms, float* cval, cudaStream_t st) {
+                                     bool correct, const float* mu, const float* wts, void* hi,
+                                     void* lo, double* norms, float* cval, cudaStream_t st) {
   const int blocks = (rows + 7) / 8;
   if (correct)
     prep_split_series_kernel<true><<<blocks, 256, 0, st>>>(
-        sr, rows, D, groups, mu, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo),
-        norms, cval);
+        sr, rows, D, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
+        static_cast<__nv_bfloat16*>(lo), norms, cval);
   else
     prep_split_series_kernel<false><<<blocks, 256, 0, st>>>(
-        sr, rows, D, groups, mu, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo),
-        norms, cval);
+        sr, rows, D, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
+        static_cast<__nv_bfloat16*>(lo), norms, cval);
   return cudaGetLastError();
 }
 
@@ -490,9 +493,9 @@ cudaError_t launch_col_mean(const float* X, int N, int D, float* partial, float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_fp32(const float* X, int N, int D, int Dp, const float* mu, float* Xc,
-                             double* norms, cudaStream_t st) {
-  prep_fp32_kernel<<<N, 256, 0, st>>>(X, D, Dp, mu, Xc, norms);
+cudaError_t launch_prep_fp32(const float* X, int N, int D, int Dp, const float* mu,
+                             const float* wts, float* Xc, double* norms, cudaStream_t st) {
+  prep_fp32_kernel<<<N, 256, 0, st>>>(X, D, Dp, mu, wts, Xc, norms);
   return cudaGetLastError();
 }
 
@@ -507,6 +510,68 @@ cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* s
   const int blocks = (a.sch.M + warps_per_block - 1) / warps_per_block;
   merge_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(a.part_d, a.part_i, a.sch.M,
                                                         a.sch.chunks, a.sch.k, idx, dist, score);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- kNN statistics
+
+namespace {
+
+// One thread per row of sorted squared distances dist[M][k]:
+//   prefix[t][k'-1] = (1/k') sum_{j<k'} dist[t][j], k' = 1..k   (Eq. 3 at every k' <= k;
+//                     the neighbour sets are nested in k, Sec. 6)
+//   local_id[t]     = [ (1/(k_id-1)) sum_{j<k_id-1} log(T_{k_id} / T_j) ]^(-1), T = sqrt(dist)
+//                     (maximum-likelihood kNN estimator of Levina and Bickel, as used in the
+//                     intrinsic dimension study of Sec. 4); NaN when a distance among the
+//                     first k_id is zero or all of them are equal.
+// Sums are FP64 (the mean's final division and the logarithm of each distance ratio
+// are FP32). A block
+// stages its 128 rows through shared memory so that global loads and stores are
+// coalesced (row pitch k + 1 avoids bank conflicts).
+constexpr int kStatRows = 128;
+
+__global__ void __launch_bounds__(kStatRows)
+    knn_stats_kernel(const float* __restrict__ dist, int M, int k, float* __restrict__ prefix,
+                     int k_id, float* __restrict__ lid) {
+  extern __shared__ float tile[];  // [kStatRows][k + 1]
+  const int r0 = blockIdx.x * kStatRows;
+  const int rows = min(kStatRows, M - r0);
+  const int pitch = k + 1;
+  for (int i = threadIdx.x; i < rows * k; i += kStatRows)
+    tile[(i / k) * pitch + i % k] = dist[(size_t)r0 * k + i];
+  __syncthreads();
+  const int r = threadIdx.x;
+  float* d = tile + r * pitch;
+  float out_id = CUDART_NAN_F;
+  if (r < rows && lid) {
+    if (d[0] > 0.f) {
+      double s = 0.0;
+      for (int j = 0; j < k_id - 1; ++j) s += 0.5 * (double)logf(d[k_id - 1] / d[j]);
+      if (s > 0.0) out_id = (float)((double)(k_id - 1) / s);
+    }
+  }
+  if (r < rows && prefix) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) {
+      s += (double)d[j];
+      d[j] = (float)s / (float)(j + 1);  // in place: d[j] is not read again
+    }
+  }
+  __syncthreads();
+  if (prefix)
+    for (int i = threadIdx.x; i < rows * k; i += kStatRows)
+      prefix[(size_t)r0 * k + i] = tile[(i / k) * pitch + i % k];
+  if (lid && r < rows) lid[r0 + r] = out_id;
+}
+
+}  // namespace
+
+cudaError_t launch_knn_stats(const float* dist, int M, int k, float* prefix, int k_id,
+                             float* local_id, cudaStream_t st) {
+  if (M < 1) return cudaSuccess;
+  const size_t smem = (size_t)kStatRows * (k + 1) * sizeof(float);
+  knn_stats_kernel<<<(M + kStatRows - 1) / kStatRows, kStatRows, smem, st>>>(dist, M, k, prefix,
+                                                                             k_id, local_id);
   return cudaGetLastError();
 }
 

@@ -127,7 +127,7 @@ extern "C" traknn_status traknn_knn_scores_static(const float* X, int64_t N, int
   // byte a kernel reads is written earlier in this same call
   if (cudaMemsetAsync(a.err, 0, sizeof(int), cs) != cudaSuccess ||
       launch_col_mean(X, (int)N, (int)D, partial, mu, true, cs) != cudaSuccess ||
-      launch_prep_fp32(X, (int)N, (int)D, Dp, mu, Xc, norms, cs) != cudaSuccess ||
+      launch_prep_fp32(X, (int)N, (int)D, Dp, mu, nullptr, Xc, norms, cs) != cudaSuccess ||
       launch_window(norms, M, L, W, cs) != cudaSuccess ||
       launch_fused_fp32(Xc, a, sms, cs) != cudaSuccess ||
       launch_merge(a, nbr_idx, nbr_dist, score, cs) != cudaSuccess) {

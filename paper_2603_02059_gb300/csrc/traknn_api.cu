@@ -79,6 +79,8 @@ struct traknn_ctx {
   int seg_k = kSegmentK;
   int group_strips = 0;
   int l2_keep_a = 0;
+  const float* weights = nullptr;  // [weights_D] grid-point weights (caller-owned), or null
+  int64_t weights_D = 0;
   int stats = 0;
   unsigned long long* stats_dev = nullptr;
   TcPlan plan;
@@ -410,7 +412,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
 
   const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
   TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
-  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, b.Dp / 64, split, b.mu, b.hi, b.lo,
+  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, b.Dp / 64, split, b.mu, h->weights,
+                                    b.hi, b.lo,
                                     b.norms, b.cval, s));
   TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s));
   TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
@@ -510,6 +513,7 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
     key.push_back((int64_t)reinterpret_cast<uintptr_t>(sd[b].score));
   }
   key.push_back(h->stats);
+  key.push_back((int64_t)reinterpret_cast<uintptr_t>(h->weights));
   key.push_back(h->debug_withhold);
   key.push_back(h->wait_limit_ms);
   for (auto& g : h->graphs)
@@ -692,6 +696,7 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   TRY_ST(check_handle(h));
   if (!X || !nbr_idx || !nbr_dist || !score) return TRAKNN_ERR_INVALID_ARG;
   TRY_ST(traknn_check_problem(N, D, L, k, e));
+  if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->precision != TRAKNN_PREC_FP32) {
     const HostSeries sd{X, N, L, k, e, nbr_idx, nbr_dist, score};
@@ -720,7 +725,7 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   fa.wait_limit_ns = (long long)h->wait_limit_ms * 1000000LL;
   fa.debug_withhold = h->debug_withhold;
   TRY_CUDA(launch_col_mean(X, (int)N, (int)D, partial, mu, h->center != 0, s));
-  TRY_CUDA(launch_prep_fp32(X, (int)N, (int)D, lay.Dp, mu, Xc, norms, s));
+  TRY_CUDA(launch_prep_fp32(X, (int)N, (int)D, lay.Dp, mu, h->weights, Xc, norms, s));
   TRY_CUDA(launch_window(norms, M, L, W, s));
   const int slot = h->ev_head;
   if (h->profile) TRY_CUDA(cudaEventRecord(h->ev_start[slot], s));
@@ -744,6 +749,7 @@ traknn_status traknn_knn_scores_batched(traknn_handle h, const traknn_series* se
     sd[b] = HostSeries{series[b].X, series[b].N, series[b].L, series[b].k, series[b].exclusion,
                        series[b].nbr_idx, series[b].nbr_dist, series[b].score};
   TRY_ST(validate_series(sd.data(), B, D));
+  if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->precision == TRAKNN_PREC_FP32) {
     for (int b = 0; b < B; ++b)
@@ -753,6 +759,27 @@ traknn_status traknn_knn_scores_batched(traknn_handle h, const traknn_series* se
   }
   for (int b0 = 0; b0 < B; b0 += kMaxSeries)
     TRY_ST(run_tc(h, sd.data() + b0, std::min(kMaxSeries, B - b0), D, s, true));
+  return TRAKNN_OK;
+}
+
+traknn_status traknn_set_grid_weights(traknn_handle h, const float* weights, int64_t D) {
+  if (!h) return TRAKNN_ERR_INVALID_ARG;
+  if (weights && (D < 1 || D > INT_MAX / 2)) return TRAKNN_ERR_INVALID_ARG;
+  h->weights = weights;
+  h->weights_D = weights ? D : 0;
+  return TRAKNN_OK;
+}
+
+traknn_status traknn_knn_stats(traknn_handle h, const float* nbr_dist, int64_t M, int k,
+                               float* prefix_scores, int k_id, float* local_id, void* stream) {
+  TRY_ST(check_handle(h));
+  if (!nbr_dist || M < 1 || M > INT_MAX / 2 || k < 1 || k > TRAKNN_MAX_K)
+    return TRAKNN_ERR_INVALID_ARG;
+  if (!prefix_scores && !local_id) return TRAKNN_ERR_INVALID_ARG;
+  if (local_id && (k_id < 2 || k_id > k)) return TRAKNN_ERR_INVALID_ARG;
+  TRY_CUDA(launch_knn_stats(nbr_dist, (int)M, k, prefix_scores, k_id, local_id,
+                            static_cast<cudaStream_t>(stream)));
+  h->launches += 1;
   return TRAKNN_OK;
 }
 
@@ -797,7 +824,9 @@ traknn_status traknn_score_backward(traknn_handle h, const float* X, int64_t N, 
   const int M = (int)(N - L + 1);
   TRY_ST(ensure_buffer(h, &h->adj, &h->adj_bytes, adjoint_workspace_bytes(M, k)));
   int launches = 0;
-  TRY_CUDA(launch_adjoint(X, (int)N, (int)D, L, k, nbr_idx, grad_score, dX, h->adj, h->err,
+  if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
+  TRY_CUDA(launch_adjoint(X, (int)N, (int)D, L, k, nbr_idx, grad_score, h->weights, dX, h->adj,
+                          h->err,
                           static_cast<cudaStream_t>(stream), &launches));
   h->launches += launches;
   return TRAKNN_OK;
