@@ -376,13 +376,20 @@ def suite_precision(args):
                     "tensor_tflops": ach,
                     "frac_sustained": ach / peaks["bf16_tflops_sustained"] if ach else None,
                     "frac_burst": ach / peaks["bf16_tflops"] if ach else None})
+    # all four trajectory lengths from one Gram sweep
+    settings = [(r["L"], r["k"], r["exclusion"]) for r in out]
+    ms_multi = _events_ms(lambda: tk.knn_scores_multi(Xd, settings, handle=h), args.steps, 3)
+    pairs_all = sum(float(N - r["L"] + 1) ** 2 for r in out)
+    multi = {"settings": settings, "ms_per_step": ms_multi,
+             "pairs_per_s": pairs_all / (ms_multi * 1e-3),
+             "sum_of_single_ms": sum(r["ms_per_step"] for r in out)}
     L, k = 5, cfg["k"]
     M = N - L + 1
     ms32 = _events_ms(lambda: tk.knn_scores(Xd, L, k, L - 1, precision="fp32", handle=h), 1, 1)
     if h.sync_status() != 0:
         raise RuntimeError("device-side failure")
     return {"suite": "precision_sweep", "workload": f"euro_75y_181x321: N={N}, D={D}",
-            "split_bf16": out,
+            "split_bf16": out, "multi_L_one_sweep": multi,
             "fp32_L5": {"ms_per_step": ms32, "pairs_per_s": float(M) * M / (ms32 * 1e-3)},
             "peak_source": src}
 
@@ -501,6 +508,12 @@ def suite_ext(args):
     peaks, src = measured_peaks()
     nbytes = M * k * 4 * 2 + M * 4
     gbs = nbytes / (ms_stats * 1e-3) / 1e9
+    # trajectory lengths 3, 5, 7, 10 from one Gram sweep on this workload
+    settings = [(Lx, k, Lx - 1) for Lx in (3, 5, 7, 10)]
+    ms_single = sum(_events_ms(lambda Lx=Lx: tk.knn_scores(Xd, Lx, k, Lx - 1, handle=h),
+                               args.steps, 3) for Lx, _, _ in settings)
+    ms_multi = _events_ms(lambda: tk.knn_scores_multi(Xd, settings, handle=h), args.steps, 3)
+    multi = {"settings": settings, "ms_per_step": ms_multi, "sum_of_single_ms": ms_single}
     # small-D form: 75 years of 32-value fields (a stand-in for PCA-reduced data)
     from synth import make_slp_like
     Xs, _ = make_slp_like(N, 4, 8, seed=20260310, annual_amp=5.0)
@@ -516,6 +529,7 @@ def suite_ext(args):
             "forward_ms": ms_plain, "forward_weighted_ms": ms_w,
             "stats_ms": ms_stats, "stats_bytes": nbytes, "stats_gbs": gbs,
             "stats_frac_hbm": gbs / peaks["hbm_gbs"], "peak_source": src,
+            "multi_L_one_sweep": multi,
             "small_D": {"workload": f"N={N}, D=32 (4x8), L={L}, k={k}", **small}}
 
 

@@ -168,6 +168,22 @@ typedef struct {
 traknn_status traknn_knn_scores_batched(traknn_handle handle, const traknn_series* series, int B,
                                         int64_t D, void* stream);
 
+/* Several (L, k, exclusion) settings of ONE record in one Gram sweep (Sec. 6: the
+ * "what-if" analyses over trajectory lengths). All nset entries must share X and N
+ * (the same device pointer and day count; D as given) and differ in L, k, exclusion
+ * and their output buffers (layouts as in traknn_knn_scores). With a tensor-core
+ * precision the Gram tiles are computed once (strip height and tile step sized for
+ * the largest L) and every tile is scanned once per setting, so the cost is close to
+ * that of one setting when the contraction dominates (large D). Each setting's
+ * outputs equal those of traknn_knn_scores on it alone except that, as in that call,
+ * D(t,j) may be evaluated from either operand order: distances agree to a few ulp
+ * and neighbour sets may differ only at near ties. With TRAKNN_PREC_FP32 the settings
+ * run one after another. 1 <= nset <= 64; each entry is checked as
+ * traknn_check_problem would check it; entries with another X or N are refused
+ * (TRAKNN_ERR_INVALID_ARG). */
+traknn_status traknn_knn_scores_multi(traknn_handle handle, const traknn_series* settings,
+                                      int nset, int64_t D, void* stream);
+
 /* Grid-point weights: with weights w (D values >= 0, DEVICE pointer, caller-owned,
  * read by every later call on this handle until cleared) the snapshot distance of
  * Eq. 2 becomes sum_p w_p (X[a,p] - X[b,p])^2 in every forward path of the handle

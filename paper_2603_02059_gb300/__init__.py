@@ -71,6 +71,7 @@ def lib():
                 "traknn_stats_read": [P, P, I],
                 "traknn_knn_scores_batched": [P, P, I, I64, P],
                 "traknn_set_grid_weights": [P, P, I64],
+                "traknn_knn_scores_multi": [P, P, I, I64, P],
                 "traknn_knn_stats": [P, P, I64, I, P, I, P, P],
             }
             for name, args in sig.items():
@@ -265,6 +266,34 @@ def knn_scores_batched(series, *, precision: str = "split_bf16", center: bool = 
     rc = lib().traknn_knn_scores_batched(h._h, ctypes.cast(arr, ctypes.c_void_p), len(series),
                                          D, ctypes.c_void_p(s.cuda_stream))
     _check(rc, "traknn_knn_scores_batched")
+    return results
+
+
+def knn_scores_multi(X: torch.Tensor, settings, *, precision: str = "split_bf16",
+                     center: bool = True, symmetric: bool = True,
+                     handle: Handle | None = None):
+    """Several (L, k, exclusion) settings of one record X ([N, D] float32 CUDA) in one
+    Gram sweep. `settings` is a list of (L, k, exclusion) (exclusion None = L - 1).
+    Returns a list of (idx, dist, score), one per setting, in the given order."""
+    X = _as_input(X)
+    N, D = X.shape
+    h = handle or get_handle(X.device.index)
+    h.configure(precision=precision, center=center, symmetric=symmetric, unit_cols=0)
+    arr = (Series * len(settings))()
+    results = []
+    for b, (L, k, exclusion) in enumerate(settings):
+        e = L - 1 if exclusion is None else int(exclusion)
+        M = max(N - L + 1, 0)
+        idx = torch.empty((M, k), dtype=torch.int32, device=X.device)
+        dist = torch.empty((M, k), dtype=torch.float32, device=X.device)
+        score = torch.empty((M,), dtype=torch.float32, device=X.device)
+        arr[b] = Series(X.data_ptr(), N, L, k, e, idx.data_ptr(), dist.data_ptr(),
+                        score.data_ptr())
+        results.append((idx, dist, score))
+    s = torch.cuda.current_stream(X.device)
+    rc = lib().traknn_knn_scores_multi(h._h, ctypes.cast(arr, ctypes.c_void_p), len(settings),
+                                       D, ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_scores_multi")
     return results
 
 

@@ -79,7 +79,8 @@ struct FusedArgs {
 struct SeriesInfo {
   int N, M, L, k;
   int e;
-  int rows_out;         // output rows per strip: 128 - (L-1)
+  int rows_out;         // output rows per strip: 128 - (L-1), or less when series share tiles
+  int step;             // output columns per Gram tile: 256 - (L-1), or less likewise
   int row_base;         // first stacked operand row (day 0 of the series)
   int out_base;         // first stacked trajectory row
   int slots;            // row-side list slots per trajectory row
@@ -107,12 +108,12 @@ struct SeriesTable {
 // collect candidates, beyond it every tile also gives each column j the strip's
 // rows as candidates (the column side), so every unordered pair is evaluated once.
 struct WorkUnit {
-  int series;
-  int strip;  // row strip; output rows [strip*rows_out, (strip+1)*rows_out)
-  int jlo;    // first output column
-  int jhi;    // one past the last output column
-  int slot;   // slot of the row-side partial lists written by this unit
-  int pad[3];
+  int series;  // first (or only) series of the unit
+  int strip;   // row strip; output rows [strip*rows_out, (strip+1)*rows_out)
+  int jlo;     // first output column
+  int jhi;     // one past the last output column (clipped to each series' M)
+  int slot;    // slot of the row-side partial lists written by this unit
+  int pad[3];  // pad[0]: number of consecutive series sharing the unit's Gram tiles
 };
 
 struct TcWork {

@@ -142,16 +142,19 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, cons
 
 // A unit with its series' parameters.
 struct UnitSpan {
-  int strip, T0, jlo, jhi, ntiles, slot;
+  int strip, T0, jlo, jhi, ntiles, slot, nser, step;
   int M, L, k, e, R;      // series: trajectories, length, neighbours, exclusion, rows per strip
   int row_base, out_base, slots, strip_base;
   long long part_base, col_base;
 };
 
-__device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr, int u,
+// Unit u for the sj-th of the series that share its Gram tiles (sj = 0: the one
+// with the most trajectories, whose tiles cover the others').
+__device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr, int u, int sj,
                                           UnitSpan& us) {
   const WorkUnit wu = w.units[u];
-  const SeriesInfo& si = sr[wu.series];
+  const SeriesInfo& si = sr[wu.series + sj];
+  us.nser = wu.pad[0] > 1 ? wu.pad[0] : 1;
   us.M = si.M;
   us.L = si.L;
   us.k = si.k;
@@ -166,13 +169,13 @@ __device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr,
   us.strip = wu.strip;
   us.T0 = wu.strip * us.R;
   us.jlo = wu.jlo;
-  us.jhi = wu.jhi;
+  us.jhi = min(wu.jhi, si.M);
   us.slot = wu.slot;
+  us.step = si.step;
   if (us.jlo >= us.jhi) return false;
-  // tiles overlap by L-1 Gram columns so that each one holds the whole window of
-  // its BN - (L-1) output columns
-  const int step = BN - (us.L - 1);
-  us.ntiles = (us.jhi - us.jlo + step - 1) / step;
+  // tiles overlap by at least L-1 Gram columns so that each one holds the whole
+  // window of its `step` output columns
+  us.ntiles = (us.jhi - us.jlo + us.step - 1) / us.step;
   return true;
 }
 
@@ -299,9 +302,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           qphase ^= 1u;
         }
         if (u >= w.nunits) break;
-        if (!unit_span(w, p.sr.s, u, us)) continue;
+        if (!unit_span(w, p.sr.s, u, 0, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
-          const int c0 = us.row_base + us.jlo + it * (BN - (us.L - 1));
+          const int c0 = us.row_base + us.jlo + it * us.step;
           const int a0 = us.row_base + us.T0;
           for (int kb = 0; kb < nkb; ++kb) {
             if (!wait_bounded(empty0 + 8u * stage, phase ^ 1u, ctl)) {
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           qphase ^= 1u;
         }
         if (u >= w.nunits) break;
-        if (!unit_span(w, p.sr.s, u, us)) continue;
+        if (!unit_span(w, p.sr.s, u, 0, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it, ++gt) {
           for (int kb = 0; kb < nkb; ++kb) {
             if (kb % seg_kb == 0) {
@@ -539,21 +542,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         qphase ^= 1u;
       }
       if (u >= w.nunits) break;
-      if (!unit_span(w, p.sr.s, u, us)) continue;
-      const int L = us.L;
-      const int LDG = chunk_pitch(L);
-      const int t = us.T0 + l;
-      const bool row_ok = l < us.R && t < us.M;
-      const float Wt = row_ok ? a.W[us.out_base + t] : 0.f;
-      // the operand layout subtracts groups * c_a * c_b from every Gram entry (see the
-      // operand preparation); it is added back when a chunk is staged, for every
-      // accumulator row whose day exists (halo rows feed other rows' windows)
-      const int N = us.M + us.L - 1;
-      const float crow = t < N ? (float)a.groups * a.cval[us.row_base + t] : 0.f;
-      const int jsym = us.T0 + us.R;  // column side from here on (sym)
-      const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
-      list.reset();
-      for (int it = 0; it < us.ntiles; ++it, ++gt) {
+      if (!unit_span(w, p.sr.s, u, 0, us)) continue;
+      // Series that share this unit's Gram tiles (several trajectory lengths of one
+      // record) are served one after another from the same accumulator; their units
+      // are one tile long, so their row lists live for one tile.
+      const int nser = us.nser;
+      const int ntiles = us.ntiles;
+      for (int it = 0; it < ntiles; ++it, ++gt) {
         lap(6);
         // the earlier segments are folded into the scratch partial total; the last
         // one is read from its accumulator while the tile is scanned
@@ -569,7 +564,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::tc_fence_after();
         lap(0);
-        const int c0 = us.jlo + it * (BN - (L - 1));
+        bool released = false;
+        for (int sj = 0; sj < nser; ++sj) {
+        if (nser > 1 && !unit_span(w, p.sr.s, u, sj, us)) continue;
+        const int L = us.L;
+        const int LDG = chunk_pitch(L);
+        const int t = us.T0 + l;
+        const bool row_ok = l < us.R && t < us.M;
+        const float Wt = row_ok ? a.W[us.out_base + t] : 0.f;
+        // the operand layout subtracts groups * c_a * c_b from every Gram entry (see the
+        // operand preparation); it is added back when a chunk is staged, for every
+        // accumulator row whose day exists (halo rows feed other rows' windows)
+        const int N = us.M + us.L - 1;
+        const float crow = t < N ? (float)a.groups * a.cval[us.row_base + t] : 0.f;
+        const int jsym = us.T0 + us.R;  // column side from here on (sym)
+        const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
+        if (nser > 1 || it == 0) list.reset();
+        const int c0 = us.jlo + it * us.step;
         // W and row bounds of this tile's output columns j = c0 - (L-1) + x (the
         // previous tile's readers passed its last barrier)
         for (int x = et; x < BN; x += kEpiThreads) {
@@ -617,10 +628,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             else
               load_scr(gt, ch + 1, vr);
           }
-          if (ch == BN / 32 - 1) {
+          if (ch == BN / 32 - 1 && sj == nser - 1) {
             // the accumulator has been read out: hand it back to the MMA warp
             ptx::tc_fence_before();
             ptx::mbar_arrive(tempty0 + 8u * acc_l);
+            released = true;
           }
           lap(2);
           ptx::named_bar_sync(bar, kEpiThreads);
@@ -777,18 +789,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float kth = kth_of(list, us.k);
           if (kth < thr_row) publish_bound(w.thr + us.out_base + t, kth);
         }
-      }
-      if (!ok) break;
-      if (row_ok && w.write_lists) {
-        const size_t base = (size_t)(us.part_base + (long long)t * us.slots + us.slot) * w.kstride;
+        if (row_ok && w.write_lists && (nser > 1 || it == ntiles - 1)) {
+          const size_t base =
+              (size_t)(us.part_base + (long long)t * us.slots + us.slot) * w.kstride;
 #pragma unroll
-        for (int pp = 0; pp < K; ++pp) {
-          if (pp < us.k) {
-            a.part_d[base + pp] = list.d[pp];
-            a.part_i[base + pp] = list.i[pp];
+          for (int pp = 0; pp < K; ++pp) {
+            if (pp < us.k) {
+              a.part_d[base + pp] = list.d[pp];
+              a.part_i[base + pp] = list.i[pp];
+            }
           }
         }
+        // the next series restages the chunk buffer and the tile's W, bounds, masks
+        if (nser > 1) ptx::named_bar_sync(bar, kEpiThreads);
+        }  // series sharing the tile
+        if (!released) {
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(tempty0 + 8u * acc_l);
+        }
       }
+      if (!ok) break;
     }
     if (w.stats) {
 #pragma unroll

@@ -187,8 +187,14 @@ static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 // are ordered per series in groups of strips that run side by side (sharing A and
 // B tiles in L2), the groups from the last strip upwards. The band units (two
 // tiles of columns centred on each strip's rows) seed the row bounds first.
+//
+// With `shared` set the B series are several (L, k, exclusion) settings of one record
+// (same X and N, sorted by ascending L): they share one set of operand rows and every
+// Gram tile, so the strip height and the tile step are those of the largest L, every
+// unit is one tile long and carries all B series (pad[0] = B), and the first series
+// (smallest L, most trajectories) defines the units' column ranges.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
-                int group_opt, TcPlan& p) {
+                int group_opt, bool shared, TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
@@ -198,12 +204,16 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
   p.kmax = 0;
   p.Lmax = 1;
   p.table.n = B;
+  int Lshare = 1;
+  for (int b = 0; b < B; ++b) Lshare = std::max(Lshare, sd[b].L);
   for (int b = 0; b < B; ++b) {
     const int N = (int)sd[b].N, L = sd[b].L, k = sd[b].k;
     const int M = N - L + 1;
-    const int R = kTileRows - (L - 1);
+    const int Lg = shared ? Lshare : L;  // geometry: strip height and tile step
+    const int R = kTileRows - (Lg - 1);
+    const int step = kTileCols - (Lg - 1);
     const int strips = (M + R - 1) / R;
-    const int cols = cols_opt > 0 ? cols_opt : tiles * (kTileCols - (L - 1));
+    const int cols = shared ? step : cols_opt > 0 ? cols_opt : tiles * step;
     const int slots = (M + cols - 1) / cols;
     SeriesInfo& si = p.table.s[b];
     si.N = N;
@@ -212,6 +222,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     si.k = k;
     si.e = sd[b].e;
     si.rows_out = R;
+    si.step = step;
     si.row_base = row_base;
     si.out_base = out_base;
     si.slots = slots;
@@ -225,27 +236,30 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
       if (sym && first_col < M) off += M - first_col;
       p.slot_lo.push_back(sym ? (s * R) / cols : 0);
     }
-    const int group = std::max(1, std::min(strips, group_opt > 0 ? group_opt : 19));
-    const int ngroups = (strips + group - 1) / group;
-    for (int gi = 0; gi < ngroups; ++gi) {
-      const int g = sym ? ngroups - 1 - gi : gi;
-      const int s_lo = g * group, s_hi = std::min(strips, s_lo + group);
-      for (int c = 0; c < slots; ++c)
-        for (int s = s_lo; s < s_hi; ++s) {
-          int jlo = c * cols;
-          const int jhi = std::min(M, (c + 1) * cols);
-          if (sym) jlo = std::max(jlo, s * R);
-          if (jlo < jhi) p.units.push_back(WorkUnit{b, s, jlo, jhi, c, {0, 0, 0}});
-        }
+    const int nser = shared ? B : 1;
+    if (!shared || b == 0) {
+      const int group = std::max(1, std::min(strips, group_opt > 0 ? group_opt : 19));
+      const int ngroups = (strips + group - 1) / group;
+      for (int gi = 0; gi < ngroups; ++gi) {
+        const int g = sym ? ngroups - 1 - gi : gi;
+        const int s_lo = g * group, s_hi = std::min(strips, s_lo + group);
+        for (int c = 0; c < slots; ++c)
+          for (int s = s_lo; s < s_hi; ++s) {
+            int jlo = c * cols;
+            const int jhi = std::min(M, (c + 1) * cols);
+            if (sym) jlo = std::max(jlo, s * R);
+            if (jlo < jhi) p.units.push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
+          }
+      }
+      // band: two tiles of columns centred on the strip's rows
+      const int bw = std::max(0, (2 * kTileCols - (Lg - 1) - R) / 2);
+      for (int s = 0; s < strips; ++s) {
+        const int T0 = s * R;
+        const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
+        if (jlo < jhi) band.push_back(WorkUnit{b, s, jlo, jhi, 0, {nser, 0, 0}});
+      }
     }
-    // band: two tiles of columns centred on the strip's rows
-    const int bw = std::max(0, (2 * kTileCols - (L - 1) - R) / 2);
-    for (int s = 0; s < strips; ++s) {
-      const int T0 = s * R;
-      const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
-      if (jlo < jhi) band.push_back(WorkUnit{b, s, jlo, jhi, 0, {0, 0, 0}});
-    }
-    row_base += N;
+    if (!shared || b == B - 1) row_base += N;
     out_base += M;
     strip_base += strips;
     part_base += (long long)M * slots;
@@ -335,12 +349,14 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
 // Make h->plan the plan for these series (built and uploaded when the shape changes)
 // and size the workspace. Must not run during a stream capture.
 traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
+                         bool shared,
                          cudaStream_t s, TcBuffers* out) {
   std::vector<int64_t> key = shape_key(sd, B, D, h);
   key.push_back(tiles);
+  key.push_back(shared ? 1 : 0);
   TcPlan& p = h->plan;
   if (p.key != key) {
-    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, p);
+    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, p);
     p.key = key;
     const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
     const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
@@ -474,7 +490,7 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   int best_t = 8;
   for (int cand : {4, 8, 16}) {
     TcBuffers buf;
-    TRY_ST(prepare_tc(h, sd, B, D, cand, s, &buf));
+    TRY_ST(prepare_tc(h, sd, B, D, cand, false, s, &buf));
     TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
     TRY_CUDA(cudaEventRecord(e0, s));
     TRY_ST(enqueue_tc(h, buf, D, s, false));
@@ -497,12 +513,12 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
 // Forward pass of B series on the tensor cores. With `graph` set the launch
 // sequence is captured once per (shape, pointers, options) and replayed.
 traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
-                     bool graph) {
+                     bool graph, bool shared = false) {
   if (!tc_available()) return TRAKNN_ERR_UNSUPPORTED;
   int tiles = 8;
-  TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
+  if (!shared) TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
   TcBuffers buf;
-  TRY_ST(prepare_tc(h, sd, B, D, tiles, s, &buf));
+  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, s, &buf));
   if (!graph) return enqueue_tc(h, buf, D, s, h->profile != 0);
 
   std::vector<int64_t> key = h->plan.key;
@@ -760,6 +776,32 @@ traknn_status traknn_knn_scores_batched(traknn_handle h, const traknn_series* se
   for (int b0 = 0; b0 < B; b0 += kMaxSeries)
     TRY_ST(run_tc(h, sd.data() + b0, std::min(kMaxSeries, B - b0), D, s, true));
   return TRAKNN_OK;
+}
+
+traknn_status traknn_knn_scores_multi(traknn_handle h, const traknn_series* settings, int nset,
+                                      int64_t D, void* stream) {
+  TRY_ST(check_handle(h));
+  if (!settings || nset < 1 || nset > kMaxSeries || D < 1) return TRAKNN_ERR_INVALID_ARG;
+  std::vector<HostSeries> sd(nset);
+  for (int b = 0; b < nset; ++b) {
+    sd[b] = HostSeries{settings[b].X, settings[b].N, settings[b].L, settings[b].k,
+                       settings[b].exclusion, settings[b].nbr_idx, settings[b].nbr_dist,
+                       settings[b].score};
+    if (sd[b].X != sd[0].X || sd[b].N != sd[0].N) return TRAKNN_ERR_INVALID_ARG;
+  }
+  TRY_ST(validate_series(sd.data(), nset, D));
+  if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->precision == TRAKNN_PREC_FP32) {
+    for (int b = 0; b < nset; ++b)
+      TRY_ST(traknn_knn_scores(h, sd[b].X, sd[b].N, D, sd[b].L, sd[b].k, sd[b].e, sd[b].idx,
+                               sd[b].dist, sd[b].score, stream));
+    return TRAKNN_OK;
+  }
+  // the shared geometry takes the smallest L (most trajectories) first
+  std::stable_sort(sd.begin(), sd.end(),
+                   [](const HostSeries& x, const HostSeries& y) { return x.L < y.L; });
+  return run_tc(h, sd.data(), nset, D, s, false, true);
 }
 
 traknn_status traknn_set_grid_weights(traknn_handle h, const float* weights, int64_t D) {
