@@ -155,52 +155,36 @@ __global__ void __launch_bounds__(256)
   }
   const float* x = si.X + (size_t)a * D;
   const float* m = mu + (size_t)b * D;
-  // FP64 norm of the centred row: FP32 squares summed 8 at a time per lane
-  double acc = 0.0;
-  float part = 0.f;
-  int cnt = 0;
   // grid-point weights w_p enter the distance as sqrt(w_p) scalings of the values
   auto val = [&](int i) { return wts ? (x[i] - m[i]) * sqrtf(wts[i]) : x[i] - m[i]; };
-  for (int q = lane; q < D; q += 32) {
-    const float v = val(q);
-    part = fmaf(v, v, part);
-    if (++cnt == 8) {
-      acc += (double)part;
-      part = 0.f;
-      cnt = 0;
-    }
-  }
-  acc += (double)part;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  const float c = kCorr ? __bfloat162float(__float2bfloat16_rn((float)sqrt(acc / groups))) : 0.f;
-  // Lane g0 + lane builds group g0 + lane: its entry pos is grid point pos * groups + g,
-  // so for each pos the warp reads 32 consecutive grid points (coalesced), and each
-  // lane then writes its group's 64 entries (128 bytes per copy) with 16-byte stores.
+  // One read of the row. Lane g0 + lane builds group g0 + lane: its entry pos is grid
+  // point pos * groups + g, so for each pos the warp reads 32 consecutive grid points
+  // (coalesced), and each lane writes its group's 64 entries (128 bytes per copy)
+  // with 16-byte stores; entry 63 (the correction) is written once the row's norm is
+  // known. The FP64 norm sums each group's FP32 squares.
+  double acc = 0.0;
   for (int g0 = 0; g0 < groups; g0 += 32) {
     const int g = g0 + lane;
     if (g >= groups) break;
     uint32_t hv[32], lv[32];  // 64 BF16 entries per copy, in pairs
+    float part = 0.f;
 #pragma unroll
     for (int pp = 0; pp < 32; ++pp) {
       const int i0 = (2 * pp) * groups + g, i1 = (2 * pp + 1) * groups + g;
       const float v0 = i0 < D ? val(i0) : 0.f;
+      const float v1 = (pp < 31 && i1 < D) ? val(i1) : 0.f;  // entry 63 filled later
+      part = fmaf(v0, v0, part);
+      part = fmaf(v1, v1, part);
       const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
       const __nv_bfloat16 q0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-      __nv_bfloat16 h1, q1;
-      if (pp == 31) {  // entry 63: the correction entry
-        h1 = __float2bfloat16_rn(c);
-        q1 = __float2bfloat16_rn(-c);
-      } else {
-        const float v1 = i1 < D ? val(i1) : 0.f;
-        h1 = __float2bfloat16_rn(v1);
-        q1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-      }
+      const __nv_bfloat16 h1 = __float2bfloat16_rn(v1);
+      const __nv_bfloat16 q1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
       const __nv_bfloat162 hp = __halves2bfloat162(h0, h1);
       const __nv_bfloat162 lp = __halves2bfloat162(q0, q1);
       hv[pp] = *reinterpret_cast<const uint32_t*>(&hp);
       lv[pp] = *reinterpret_cast<const uint32_t*>(&lp);
     }
+    acc += (double)part;
     uint4* hd = reinterpret_cast<uint4*>(h2 + (size_t)g * 32);
     uint4* ld = reinterpret_cast<uint4*>(l2 + (size_t)g * 32);
 #pragma unroll
@@ -208,6 +192,16 @@ __global__ void __launch_bounds__(256)
       hd[v] = make_uint4(hv[4 * v], hv[4 * v + 1], hv[4 * v + 2], hv[4 * v + 3]);
       ld[v] = make_uint4(lv[4 * v], lv[4 * v + 1], lv[4 * v + 2], lv[4 * v + 3]);
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const float c = kCorr ? __bfloat162float(__float2bfloat16_rn((float)sqrt(acc / groups))) : 0.f;
+  // the correction entries of this lane's groups (same thread as the stores above)
+  __nv_bfloat16* hrow = hi + (size_t)r * Dp;
+  __nv_bfloat16* lrow = lo + (size_t)r * Dp;
+  for (int g = lane; g < groups; g += 32) {
+    hrow[g * 64 + 63] = __float2bfloat16_rn(c);
+    lrow[g * 64 + 63] = __float2bfloat16_rn(-c);
   }
   if (lane == 0) {
     norms[r] = acc;
