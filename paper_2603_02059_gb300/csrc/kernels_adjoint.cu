@@ -95,54 +95,171 @@ __global__ void adj_sort_kernel(const int* __restrict__ off, int M, int* rev) {
 }
 
 constexpr int kGatherThreads = 256;
+constexpr int kMaxInc = 2048;                       // incidences merged in shared memory
+constexpr int kPerThread = kMaxInc / kGatherThreads;  // consecutive positions per thread
 
-// One CTA per day a: dX[a] = sum over incidences w (X[a] - X[b]), fixed order
-// (forward incidences by t then neighbour rank, then reverse ones by j then t).
+// One CTA per day a: dX[a] = sum over incidences w (X[a] - X[b]).
+//
+// The incidences (forward: by t, then neighbour rank; reverse: by j, then t) are
+// listed in shared memory as keys (partner day b, position in that order) and
+// sorted; the weights of each partner are summed in the listed order and the
+// partners are visited in increasing day order, so every partner row X[b] is read
+// once (consecutive days tend to have consecutive neighbours, so a day's incidences
+// have about half as many distinct partners). A day with more incidences than the
+// buffer holds sums them one by one in the listed order instead. Both ways the
+// order is fixed, so the result is bitwise reproducible.
 __global__ void __launch_bounds__(kGatherThreads)
     adj_gather_kernel(const float* __restrict__ X, int N, int D, int L, int M, int k,
                       const int32_t* __restrict__ idx, const float* __restrict__ g,
                       const int* __restrict__ off, const int* __restrict__ rev,
                       const float* __restrict__ wts, float* __restrict__ dX) {
+  __shared__ unsigned long long key[kMaxInc];  // (partner << 32) | position
+  __shared__ float wpos[kMaxInc];              // weight of each position
+  __shared__ float wsum[kMaxInc];              // merged weight of each distinct partner
+  __shared__ int part[kMaxInc];                // distinct partners, increasing
+  __shared__ int scan[kGatherThreads];
+  __shared__ int rstart[kMaxL + 1];            // first position of each reverse segment
   const int a = blockIdx.x;
+  const int tid = threadIdx.x;
   const float* xa = X + (size_t)a * D;
   const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
+  const int nt = max(0, t_hi - t_lo + 1);
   const float inv_k2 = 2.0f / (float)k;
+  const int nfwd = nt * k;
+  if (tid == 0) {
+    int pos = nfwd;
+    for (int j = t_lo; j <= t_hi; ++j) {
+      rstart[j - t_lo] = pos;
+      pos += off[j + 1] - off[j];
+    }
+    rstart[nt] = pos;
+  }
+  __syncthreads();
+  const int ninc = rstart[nt];
+  const bool merged = ninc <= kMaxInc;
+  int nu = 0;
+  if (merged) {
+    int n2 = 1;
+    while (n2 < ninc) n2 <<= 1;
+    for (int q = tid; q < n2; q += kGatherThreads) {
+      unsigned long long kq = ~0ull;  // padding and invalid entries sort last
+      float wq = 0.f;
+      if (q < nfwd) {
+        const int t = t_lo + q / k;
+        const int j = idx[(size_t)t * k + q % k];
+        if (j >= 0 && j < M) {
+          kq = ((unsigned long long)(unsigned)(j + a - t) << 32) | (unsigned)q;
+          wq = inv_k2 * g[t];
+        }
+      } else if (q < ninc) {
+        int sg = 0;
+        while (rstart[sg + 1] <= q) ++sg;  // reverse segment of day j = t_lo + sg
+        const int j = t_lo + sg;
+        const int t = rev[off[j] + (q - rstart[sg])];
+        kq = ((unsigned long long)(unsigned)(t + a - j) << 32) | (unsigned)q;
+        wq = inv_k2 * g[t];
+      }
+      key[q] = kq;
+      wpos[q] = wq;
+    }
+    __syncthreads();
+    // bitonic sort of the n2 keys (ascending)
+    for (int size = 2; size <= n2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int q = tid; q < n2; q += kGatherThreads) {
+          const int r = q ^ stride;
+          if (r > q) {
+            const bool up = (q & size) == 0;
+            const unsigned long long x = key[q], y = key[r];
+            if ((x > y) == up) {
+              key[q] = y;
+              key[r] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // run heads (first position of each distinct valid partner), numbered by an
+    // exclusive prefix sum over the thread's kPerThread consecutive positions
+    auto head = [&](int q) {
+      if (q >= ninc || key[q] == ~0ull) return 0;
+      return (q == 0 || (key[q - 1] >> 32) != (key[q] >> 32)) ? 1 : 0;
+    };
+    const int q0 = tid * kPerThread;
+    int cnt = 0;
+    for (int i = 0; i < kPerThread; ++i) cnt += head(q0 + i);
+    scan[tid] = cnt;
+    __syncthreads();
+    for (int o = 1; o < kGatherThreads; o <<= 1) {
+      const int v = tid >= o ? scan[tid - o] : 0;
+      __syncthreads();
+      scan[tid] += v;
+      __syncthreads();
+    }
+    int u = scan[tid] - cnt;
+    for (int i = 0; i < kPerThread; ++i) {
+      const int q = q0 + i;
+      if (!head(q)) continue;
+      const unsigned long long b = key[q] >> 32;
+      float w = 0.f;
+      for (int r = q; r < ninc && key[r] != ~0ull && (key[r] >> 32) == b; ++r)
+        w += wpos[(unsigned)key[r]];
+      part[u] = (int)b;
+      wsum[u] = w;
+      ++u;
+    }
+    nu = scan[kGatherThreads - 1];
+    __syncthreads();
+  }
   for (int p0 = 0; p0 < D; p0 += kGatherThreads * 4) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     float xv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int p = p0 + u * kGatherThreads + threadIdx.x;
+      const int p = p0 + u * kGatherThreads + tid;
       xv[u] = p < D ? xa[p] : 0.f;
     }
-    for (int t = t_lo; t <= t_hi; ++t) {
-      const float w = inv_k2 * g[t];
-      for (int i = 0; i < k; ++i) {
-        const int j = idx[(size_t)t * k + i];
-        if (j < 0 || j >= M) continue;
-        const float* xb = X + (size_t)(j + a - t) * D;
+    if (merged) {
+      for (int v = 0; v < nu; ++v) {
+        const float w = wsum[v];
+        const float* xb = X + (size_t)part[v] * D;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int p = p0 + u * kGatherThreads + threadIdx.x;
+          const int p = p0 + u * kGatherThreads + tid;
           if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
         }
       }
-    }
-    for (int j = t_lo; j <= t_hi; ++j) {
-      for (int r = off[j]; r < off[j + 1]; ++r) {
-        const int t = rev[r];
+    } else {
+      for (int t = t_lo; t <= t_hi; ++t) {
         const float w = inv_k2 * g[t];
-        const float* xb = X + (size_t)(t + a - j) * D;
+        for (int i = 0; i < k; ++i) {
+          const int j = idx[(size_t)t * k + i];
+          if (j < 0 || j >= M) continue;
+          const float* xb = X + (size_t)(j + a - t) * D;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int p = p0 + u * kGatherThreads + threadIdx.x;
-          if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
+          for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * kGatherThreads + tid;
+            if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
+          }
+        }
+      }
+      for (int j = t_lo; j <= t_hi; ++j) {
+        for (int r = off[j]; r < off[j + 1]; ++r) {
+          const int t = rev[r];
+          const float w = inv_k2 * g[t];
+          const float* xb = X + (size_t)(t + a - j) * D;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * kGatherThreads + tid;
+            if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
+          }
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int p = p0 + u * kGatherThreads + threadIdx.x;
+      const int p = p0 + u * kGatherThreads + tid;
       if (p < D) dX[(size_t)a * D + p] = wts ? acc[u] * wts[p] : acc[u];
     }
   }
