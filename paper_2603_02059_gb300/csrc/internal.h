@@ -119,7 +119,7 @@ struct WorkUnit {
 struct TcWork {
   const WorkUnit* units;
   int nunits;
-  int kstride;              // list stride (largest k of the call)
+  int kstride;              // list pitch: largest k of the call rounded up to 4
   const long long* col_off; // [stacked strips] column-list offset within the series
   const int* slot_lo;       // [stacked strips] first slot written for the strip's rows
   int sym;                  // 1: upper triangle + column side

@@ -355,22 +355,42 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
   for (int pass = 0; pass < 64; ++pass) {
     if (lane == 0) bn[wid] = 0;
     __syncwarp();
+    // lists are read four entries at a time (the list pitch ks is a multiple of 4)
     for (int c = c_lo + lane; c < si.slots; c += 32) {
       const size_t b = (size_t)(plist + c) * ks;
-      for (int p = 0; p < k; ++p) {
-        const int ii = part_i[b + p];
-        const float d = part_d[b + p];
-        if (ii < 0 || d > thr) break;
-        push(d, ii);
+      const float4* d4 = reinterpret_cast<const float4*>(part_d + b);
+      const int4* i4 = reinterpret_cast<const int4*>(part_i + b);
+      bool more = true;
+      for (int p = 0; more && p < k; p += 4) {
+        const float4 dv = __ldg(d4 + p / 4);
+        const int4 iv = __ldg(i4 + p / 4);
+        const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
+        const int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!more || p + u >= k) break;
+          if (ii[u] < 0 || dd[u] > thr) {
+            more = false;  // sorted: nothing further qualifies
+          } else {
+            push(dd[u], ii[u]);
+          }
+        }
       }
     }
     if (w.sym) {
       for (int s2 = lane; s2 < strip; s2 += 32) {
         const long long li = collist(s2);
         const int nn = w.col_n[li];
-        for (int p = 0; p < nn; ++p) {  // column lists are not sorted
-          const float d = w.col_d[li * ks + p];
-          if (d <= thr) push(d, w.col_i[li * ks + p]);
+        const float4* d4 = reinterpret_cast<const float4*>(w.col_d + li * ks);
+        const int4* i4 = reinterpret_cast<const int4*>(w.col_i + li * ks);
+        for (int p = 0; p < nn; p += 4) {  // column lists are not sorted
+          const float4 dv = __ldg(d4 + p / 4);
+          const int4 iv = __ldg(i4 + p / 4);
+          const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
+          const int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (p + u < nn && dd[u] <= thr) push(dd[u], ii[u]);
         }
       }
     }

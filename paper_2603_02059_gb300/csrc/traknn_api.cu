@@ -181,6 +181,10 @@ Layout make_layout(int64_t N, int64_t D, const Schedule& s) {
 
 static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 
+// Pitch of the candidate lists: k rounded up to 4 entries, so that every list starts
+// on a 16-byte boundary and is read four entries at a time.
+inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
+
 // Tensor-core work list of a batch. For each series: strips of 128 - (L-1) output
 // rows; units of `tiles` Gram tiles (each yielding kTileCols - (L-1) output columns);
 // with the symmetric split only columns from each strip's own block on. Units
@@ -326,7 +330,7 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
   };
   b.Dp = tc_groups((int)D) * 64;
   const int B = p.table.n;
-  const size_t ks = (size_t)p.kmax;
+  const size_t ks = (size_t)list_pitch(p.kmax);
   b.partial = reinterpret_cast<float*>(take((size_t)B * kMeanSlices * D * sizeof(float)));
   b.mu = reinterpret_cast<float*>(take((size_t)B * D * sizeof(float)));
   b.norms = reinterpret_cast<double*>(take((size_t)p.rows * sizeof(double)));
@@ -414,7 +418,7 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
   w.nunits = p.nunits;
-  w.kstride = p.kmax;
+  w.kstride = list_pitch(p.kmax);
   w.col_off = reinterpret_cast<const long long*>(pd + ub);
   w.slot_lo = reinterpret_cast<const int*>(pd + ub + cb);
   w.sym = h->sym;
