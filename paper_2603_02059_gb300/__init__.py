@@ -320,7 +320,8 @@ def knn_stats(dist: torch.Tensor, k_id: int | None = None, *, prefix: bool = Tru
 
 
 def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
-                    precision: str = "split_bf16", center: bool = True, handle=None, out=None,
+                    precision: str = "split_bf16", center: bool = True, col_chunks: int = 0,
+                    symmetric: bool = True, unit_cols: int = 0, handle=None, out=None,
                     device: int | None = None):
     """Host-buffer variant: X_host is a CPU float32 tensor (pinned for fast copies);
     returns CPU tensors. The call copies in, computes, copies out and synchronises."""
@@ -331,7 +332,8 @@ def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None 
     e = L - 1 if exclusion is None else int(exclusion)
     M = N - L + 1
     h = handle or get_handle(device)
-    h.configure(precision=precision, center=center)
+    h.configure(precision=precision, center=center, col_chunks=col_chunks, symmetric=symmetric,
+                unit_cols=unit_cols)
     if out is None:
         pin = X_host.is_pinned()
         idx = torch.empty((M, k), dtype=torch.int32, pin_memory=pin)
