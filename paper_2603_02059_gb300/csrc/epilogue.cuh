@@ -1,6 +1,6 @@
 // epilogue.cuh -- per-row work that turns a tile of the snapshot Gram matrix into
-// trajectory distances and keeps each row's k nearest candidates. Shared by the
-// FP32 CUDA-core kernel and the tcgen05 tensor-core kernel.
+// trajectory distances and keeps each row's k nearest candidates, as used by the
+// FP32 CUDA-core kernel (the tensor-core kernel has its own register-based scan).
 //
 // With day norms n_a = ||X_a||^2 and window sums W_t = sum_{m<L} n_{t+m}, the
 // trajectory distance of Eq. 2 expands (Eq. 4 applied to every day pair) into

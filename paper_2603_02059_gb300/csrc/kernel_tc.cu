@@ -9,6 +9,11 @@
 // (the lo.lo term, about 2^-16 of |x_a||x_b|, is dropped), accumulated in FP32
 // in tensor memory. The day norms and window sums stay FP64 (kernels_aux.cu).
 //
+// Operands are the grouped BF16 copies of the operand preparation (kernels_aux.cu):
+// per 64 K entries, 63 permuted grid points and one correction entry that makes the
+// accumulator hold G - groups c_a c_b (small for close pairs); the epilogue adds
+// groups c_a c_b back in FP32.
+//
 // One persistent CTA per SM, warp-specialised:
 //   warp 0   TMA producer: A (128 strip rows) and B (256 tile columns) K-chunks of
 //            32 elements into a ring of shared-memory stages (hi and lo copies);
@@ -16,16 +21,22 @@
 //            TMEM (512 columns). The K range of a tile is cut into segments
 //            (8192 elements by default); every segment accumulates afresh into
 //            the next accumulator, so segment s+1 multiplies while segment s is
-//            read out. With more than one segment per tile the epilogue adds the
-//            segments in FP32 on the CUDA cores into a running total of the tile
-//            in a per-CTA scratch array (L2-resident) and scans the tile from
-//            there: the tensor cores never accumulate more than one segment of
-//            products per output, which bounds the error of their accumulation
-//            however large D is;
+//            read out. With more than one segment per tile the epilogue adds every
+//            segment but the last, in FP32 on the CUDA cores, into a running total
+//            of the tile in a per-CTA scratch array (L2-resident), and adds the last
+//            from TMEM while scanning: the tensor cores never accumulate more than
+//            one segment of products per output, which bounds the error of their
+//            accumulation however large D is;
 //   warps 2-5 epilogue: each thread owns one accumulator row (TMEM lane), pulls
 //            32 columns at a time with tcgen05.ld, stages them beside the L-1
-//            columns carried from the previous chunk, and runs the shared
-//            window/mask/top-k scan.
+//            columns carried from the previous chunk, sums each output's window
+//            down the diagonal, masks the exclusion zone, and keeps the row's k
+//            best in registers (row side). Beyond the strip's own block the same
+//            distances are offered, transposed by warp ballots, to the columns'
+//            lists (column side), so each unordered pair is evaluated once.
+// Work units (a strip and a range of columns, or a band unit that only seeds the
+// per-row bounds) are handed out dynamically; a unit may serve several series that
+// share its Gram tiles (several trajectory lengths of one record).
 // Every wait is bounded (globaltimer); a wait that runs out records a timeout
 // in the status word, the CTA drains its own copies and MMAs, frees TMEM and
 // returns.
@@ -33,7 +44,6 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
-#include "epilogue.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
 
