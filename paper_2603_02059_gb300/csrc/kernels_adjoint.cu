@@ -79,10 +79,27 @@ __device__ void sift_down(int* a, int root, int n) {
   }
 }
 
-// Sort every reverse segment ascending (heap sort: O(n log n), in place).
-__global__ void adj_sort_kernel(const int* __restrict__ off, int M, int* rev) {
+constexpr int kMaxInc = 2048;  // incidences of one day merged in the gather's shared memory
+
+// Incidences of day a: the forward ones (k per trajectory t of its window) and the
+// reverse segments of the days j of its window, [max(0, a-L+1), min(a, M-1)].
+__device__ __forceinline__ int day_incidences(const int* off, int a, int L, int M, int k) {
+  const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
+  if (t_hi < t_lo) return 0;
+  return (t_hi - t_lo + 1) * k + (off[t_hi + 1] - off[t_lo]);
+}
+
+// Sort ascending (heap sort, in place) every reverse segment that some day reads one
+// incidence at a time: a day with more incidences than the gather's buffer, whose
+// summation order must not depend on the order the fill kernel produced. The other
+// days order their incidences by key in the gather and need no sorted segments.
+__global__ void adj_sort_kernel(const int* __restrict__ off, int N, int L, int M, int k,
+                                int* rev) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
+  bool needed = false;
+  for (int d = j; d < min(N, j + L); ++d) needed |= day_incidences(off, d, L, M, k) > kMaxInc;
+  if (!needed) return;
   int* a = rev + off[j];
   const int n = off[j + 1] - off[j];
   for (int r = n / 2 - 1; r >= 0; --r) sift_down(a, r, n);
@@ -95,18 +112,20 @@ __global__ void adj_sort_kernel(const int* __restrict__ off, int M, int* rev) {
 }
 
 constexpr int kGatherThreads = 256;
-constexpr int kMaxInc = 2048;                       // incidences merged in shared memory
 constexpr int kPerThread = kMaxInc / kGatherThreads;  // consecutive positions per thread
 
 // One CTA per day a: dX[a] = sum over incidences w (X[a] - X[b]).
 //
-// The incidences (forward: by t, then neighbour rank; reverse: by j, then t) are
-// listed in shared memory as keys (partner day b, position in that order) and
-// sorted; the weights of each partner are summed in the listed order and the
-// partners are visited in increasing day order, so every partner row X[b] is read
-// once (consecutive days tend to have consecutive neighbours, so a day's incidences
-// have about half as many distinct partners). A day with more incidences than the
-// buffer holds sums them one by one in the listed order instead. Both ways the
+// The incidences are listed in shared memory as keys (partner day b, kind, window
+// slot): a forward incidence (trajectory t, neighbour j, b = j + a - t) has kind 0
+// and slot t - t_lo, a reverse one (j in the window, t with j among its neighbours,
+// b = t + a - j) kind 1 and slot j - t_lo. For one partner no two incidences share
+// kind and slot, so the sorted order does not depend on the order the lists were
+// built in. The weights of each partner are summed in key order and the partners
+// are visited in increasing day order, so every partner row X[b] is read once
+// (consecutive days tend to have consecutive neighbours, so a day's incidences have
+// about half as many distinct partners). A day with more incidences than the buffer
+// holds sums them one by one, forward then reverse in sorted segments. Both ways the
 // order is fixed, so the result is bitwise reproducible.
 __global__ void __launch_bounds__(kGatherThreads)
     adj_gather_kernel(const float* __restrict__ X, int N, int D, int L, int M, int k,
@@ -114,7 +133,6 @@ __global__ void __launch_bounds__(kGatherThreads)
                       const int* __restrict__ off, const int* __restrict__ rev,
                       const float* __restrict__ wts, float* __restrict__ dX) {
   __shared__ unsigned long long key[kMaxInc];  // (partner << 32) | position
-  __shared__ float wpos[kMaxInc];              // weight of each position
   __shared__ float wsum[kMaxInc];              // merged weight of each distinct partner
   __shared__ int part[kMaxInc];                // distinct partners, increasing
   __shared__ int scan[kGatherThreads];
@@ -143,24 +161,19 @@ __global__ void __launch_bounds__(kGatherThreads)
     while (n2 < ninc) n2 <<= 1;
     for (int q = tid; q < n2; q += kGatherThreads) {
       unsigned long long kq = ~0ull;  // padding and invalid entries sort last
-      float wq = 0.f;
       if (q < nfwd) {
-        const int t = t_lo + q / k;
+        const int ts = q / k;
+        const int t = t_lo + ts;
         const int j = idx[(size_t)t * k + q % k];
-        if (j >= 0 && j < M) {
-          kq = ((unsigned long long)(unsigned)(j + a - t) << 32) | (unsigned)q;
-          wq = inv_k2 * g[t];
-        }
+        if (j >= 0 && j < M) kq = ((unsigned long long)(unsigned)(j + a - t) << 32) | (unsigned)ts;
       } else if (q < ninc) {
         int sg = 0;
         while (rstart[sg + 1] <= q) ++sg;  // reverse segment of day j = t_lo + sg
         const int j = t_lo + sg;
         const int t = rev[off[j] + (q - rstart[sg])];
-        kq = ((unsigned long long)(unsigned)(t + a - j) << 32) | (unsigned)q;
-        wq = inv_k2 * g[t];
+        kq = ((unsigned long long)(unsigned)(t + a - j) << 32) | (1u << 16) | (unsigned)sg;
       }
       key[q] = kq;
-      wpos[q] = wq;
     }
     __syncthreads();
     // bitonic sort of the n2 keys (ascending)
@@ -203,8 +216,13 @@ __global__ void __launch_bounds__(kGatherThreads)
       if (!head(q)) continue;
       const unsigned long long b = key[q] >> 32;
       float w = 0.f;
-      for (int r = q; r < ninc && key[r] != ~0ull && (key[r] >> 32) == b; ++r)
-        w += wpos[(unsigned)key[r]];
+      for (int r = q; r < ninc && key[r] != ~0ull && (key[r] >> 32) == b; ++r) {
+        // the incidence's trajectory t, recovered from its kind and slot
+        const unsigned lo = (unsigned)key[r];
+        const int slot = (int)(lo & 0xFFFFu);
+        const int t = (lo >> 16) ? (int)b - a + t_lo + slot : t_lo + slot;
+        w += inv_k2 * g[t];
+      }
       part[u] = (int)b;
       wsum[u] = w;
       ++u;
@@ -286,7 +304,7 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_count_kernel<<<blocks, 256, 0, st>>>(idx, M, k, count, err);
   adj_scan_kernel<<<1, 1024, 0, st>>>(count, M, off);
   adj_fill_kernel<<<blocks, 256, 0, st>>>(idx, M, k, off, cursor, rev);
-  adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, M, rev);
+  adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, N, L, M, k, rev);
   adj_gather_kernel<<<N, kGatherThreads, 0, st>>>(X, N, D, L, M, k, idx, g, off, rev, wts, dX);
   *launches += 5;
   return cudaGetLastError();
