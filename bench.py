@@ -244,7 +244,8 @@ def run_ours(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_split, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": head,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"split_bf16": "bf16", "bf16": "bf16", "fp32": "f32"}[head],
         "data": "synthetic (seeded SLP-like anomalies; one independent series per rank)",
         "config": {"workload": (f"{WORKLOAD}: N={N} days, D={D} (46x81), L={L}, k={k}, "
                                 f"exclusion={e}, M={M}"),
