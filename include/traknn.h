@@ -161,7 +161,8 @@ typedef struct {
  * With a tensor-core precision up to 64 series run in one persistent launch
  * sequence, which is captured as a CUDA graph on first use and replayed on later
  * calls with the same shapes, pointers and options (the handle keeps one graph
- * per such signature; a change of shape or a larger workspace drops them).
+ * per such signature, the 16 most recent; a change of shape or a larger workspace
+ * drops them; evicting the oldest synchronises `stream` once).
  * With TRAKNN_PREC_FP32 the series run one after another. Each series is
  * checked as traknn_check_problem would check it; the first failing series'
  * status is returned before anything is enqueued. */

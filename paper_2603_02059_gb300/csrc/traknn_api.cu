@@ -40,6 +40,8 @@ struct TcPlan {
   long long part_lists = 0, col_lists = 0;
 };
 
+constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
+
 struct GraphEntry {
   std::vector<int64_t> key;  // plan key, pointers and options
   cudaGraphExec_t exec = nullptr;
@@ -561,6 +563,12 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
   cudaGraphDestroy(g);
   TRY_CUDA(ie);
   h->launches = l0;  // the capture enqueued nothing
+  if (h->graphs.size() >= kMaxGraphs) {
+    // keep the cache bounded: drop the oldest graph (after its launches have finished)
+    TRY_CUDA(cudaStreamSynchronize(s));
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
   h->graphs.push_back(GraphEntry{key, exec});
   TRY_CUDA(cudaGraphLaunch(exec, s));
   h->launches += (h->center ? 2 : 1) + 2 + (h->plan.nband > 0 ? 1 : 0) + 2;

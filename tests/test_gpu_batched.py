@@ -127,3 +127,17 @@ def test_invalid_series_is_rejected_before_launch(tk):
         tk.knn_scores_batched(bad)
     assert ei.value.status == 2
     assert tk.get_handle().launch_count() == n0
+
+
+def test_graph_cache_stays_bounded(tk):
+    """New output buffers on every call create new graph signatures; the cache keeps
+    only the most recent ones and every call stays correct."""
+    import torch
+    shapes = SHAPES[:2]
+    Xds = [torch.from_numpy(X).cuda() for X in _series(shapes, seed0=1500)]
+    ref = [_single(tk, X, L, k, e, "split_bf16") for X, (N, L, k, e) in zip(Xds, shapes)]
+    for _ in range(20):
+        got = _batched(tk, Xds, shapes, "split_bf16")  # fresh outputs each time
+        for a, b in zip(ref, got):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
