@@ -114,3 +114,32 @@ def test_knn_stats_local_id_for_smaller_k_and_errors(tk):
         tk.knn_stats(d, k_id=5)
     with pytest.raises(tk.TrakNNError):
         tk.knn_stats(d, k_id=None, prefix=False)
+
+
+def test_weights_apply_to_batched_and_multi_calls(tk):
+    """Grid weights set on a handle act on every forward entry point: the batched and
+    the several-settings calls agree with weighted single calls."""
+    import torch
+    w = _coslat(9, 14)
+    h = tk.Handle()
+    h.set_grid_weights(torch.from_numpy(w).cuda())
+    Xs = [torch.from_numpy(make_slp_like(n, 9, 14, seed=70 + n)[0]).cuda() for n in (600, 900)]
+    singles = [tk.knn_scores(X, 4, 8, 3, handle=h) for X in Xs]
+    batched = tk.knn_scores_batched([(X, 4, 8, 3) for X in Xs], handle=h)
+    multi = tk.knn_scores_multi(Xs[1], [(4, 8, 3), (2, 6, 1)], handle=h)
+    single_l2 = tk.knn_scores(Xs[1], 2, 6, 1, handle=h)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    for ref, got in zip(singles, batched):
+        for a, b in zip(ref, got):
+            assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    for ref, got in ((singles[1], multi[0]), (single_l2, multi[1])):
+        rd, gd = ref[1].cpu().numpy(), got[1].cpu().numpy()
+        assert np.max(np.abs(rd - gd) / rd) <= 1e-6
+        assert np.allclose(ref[2].cpu().numpy(), got[2].cpu().numpy(), rtol=1e-6)
+    # and the weights matter
+    h.set_grid_weights(None)
+    plain = tk.knn_scores(Xs[0], 4, 8, 3, handle=h)
+    torch.cuda.synchronize()
+    assert not np.allclose(plain[2].cpu().numpy(), singles[0][2].cpu().numpy(), rtol=1e-3)
+    h.close()
