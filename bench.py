@@ -515,6 +515,17 @@ def suite_ext(args):
                                args.steps, 3) for Lx, _, _ in settings)
     ms_multi = _events_ms(lambda: tk.knn_scores_multi(Xd, settings, handle=h), args.steps, 3)
     multi = {"settings": settings, "ms_per_step": ms_multi, "sum_of_single_ms": ms_single}
+    # time against k (the paper notes k has little influence on the cost) and N
+    k_sweep = {}
+    for kx in (5, 10, 20, 40, 64):
+        k_sweep[kx] = _events_ms(lambda kx=kx: tk.knn_scores(Xd, L, kx, e, handle=h),
+                                 args.steps, 3)
+    n_sweep = {}
+    for nx in (6849, 13697, 20546, N):  # about 19, 37.5, 56 and 75 years
+        Xn = Xd[:nx]
+        ms = _events_ms(lambda Xn=Xn: tk.knn_scores(Xn, L, k, e, handle=h), args.steps, 3)
+        mx = nx - L + 1
+        n_sweep[nx] = {"ms_per_step": ms, "pairs_per_s": float(mx) * mx / (ms * 1e-3)}
     # small-D form: 75 years of 32-value fields (a stand-in for PCA-reduced data)
     from synth import make_slp_like
     Xs, _ = make_slp_like(N, 4, 8, seed=20260310, annual_amp=5.0)
@@ -530,7 +541,7 @@ def suite_ext(args):
             "forward_ms": ms_plain, "forward_weighted_ms": ms_w,
             "stats_ms": ms_stats, "stats_bytes": nbytes, "stats_gbs": gbs,
             "stats_frac_hbm": gbs / peaks["hbm_gbs"], "peak_source": src,
-            "multi_L_one_sweep": multi,
+            "multi_L_one_sweep": multi, "ms_vs_k": k_sweep, "ms_vs_N": n_sweep,
             "small_D": {"workload": f"N={N}, D=32 (4x8), L={L}, k={k}", **small}}
 
 

@@ -937,6 +937,8 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Tc
   if (k <= 16) return launch_k<16>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
   if (k <= 20) return launch_k<20>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
   if (k <= 32) return launch_k<32>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 40) return launch_k<40>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 48) return launch_k<48>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
   return launch_k<64>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
 }
 

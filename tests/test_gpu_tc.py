@@ -56,6 +56,7 @@ def test_small_5y_config_split(tk):
     (1000, 3, 3, 2, 9, 0),
     (777, 9, 15, 10, 20, 9),
     (1300, 16, 20, 7, 33, 6),
+    (900, 8, 10, 4, 45, 3),
 ])
 def test_shapes_split(tk, N, h, w, L, k, e):
     X, _ = make_slp_like(N, h, w, seed=N + L)
