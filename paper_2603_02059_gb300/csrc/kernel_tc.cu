@@ -607,13 +607,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         // segment, else the scratch partial total (the last segment's chunk is
         // added from TMEM when the chunk is staged)
         const uint32_t tlast = tmem_base + lane_addr + (uint32_t)(acc_l * BN);
+        // with the largest lists the chunk is fetched when it is staged instead (the
+        // prefetched registers would otherwise stay live across the scan and spill)
+        constexpr bool kAhead = K <= 40;
         uint32_t vr[32];
-        if (nseg == 1)
-          ptx::tmem_ld32_async(tlast, vr);
-        else
-          load_scr(gt, 0, vr);
+        if (kAhead) {
+          if (nseg == 1)
+            ptx::tmem_ld32_async(tlast, vr);
+          else
+            load_scr(gt, 0, vr);
+        }
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
+          if (!kAhead) {
+            if (nseg == 1)
+              ptx::tmem_ld32_async(tlast + (uint32_t)(ch * 32), vr);
+            else
+              load_scr(gt, ch, vr);
+          }
           float* grow = Gbuf + l * LDG;
           if (ch > 0)
             for (int c = 0; c < L - 1; ++c) grow[c] = grow[32 + c];
@@ -632,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               grow[(L - 1) + x] =
                   fmaf(crow, cs[x], __uint_as_float(vr[x]) + __uint_as_float(tv[x]));
           }
-          if (ch + 1 < BN / 32) {
+          if (kAhead && ch + 1 < BN / 32) {
             if (nseg == 1)
               ptx::tmem_ld32_async(tlast + (uint32_t)((ch + 1) * 32), vr);
             else
