@@ -131,6 +131,19 @@ def test_euro_75y_sampled_rows_split(tk):
         assert min(abs(t - s0) for t in top) <= L - 1
 
 
+@pytest.mark.parametrize("L,k", [(17, 64), (10, 48), (2, 1)])
+def test_euro_75y_sampled_rows_extreme_settings(tk, L, k):
+    """The 75-year workload at the largest (and the smallest) supported trajectory
+    length and neighbour count: sampled rows against the oracle."""
+    X, meta, cfg = config_inputs("euro_75y_46x81")
+    e = L - 1
+    idx, dist, score = _run(tk, X, L, k, e)
+    M = X.shape[0] - L + 1
+    rng = np.random.default_rng(L * 100 + k)
+    rows = np.unique(np.concatenate([[0, 127 - L, M - 1], rng.integers(0, M, 8)]))
+    check_sampled(X, L, k, e, rows, idx, dist, score, TOL["split_bf16"])
+
+
 def test_bounded_wait_reports_timeout(tk):
     """The producer withholds one stage (test hook): the consumer's bounded wait runs out,
     the kernel records TRAKNN_ERR_TIMEOUT and returns; the next call is correct again."""
