@@ -141,3 +141,22 @@ def test_graph_cache_stays_bounded(tk):
         for a, b in zip(ref, got):
             for x, y in zip(a, b):
                 assert np.array_equal(x, y)
+
+
+def test_batched_with_k_segments_equals_single_calls(tk):
+    """Several series whose Gram entries are accumulated in K segments (folded through
+    the per-CTA scratch): each equals its single call under the same segmenting."""
+    import torch
+    shapes = [(700, 5, 10, 4), (450, 3, 6, 2), (820, 8, 12, 7)]
+    Xds = [torch.from_numpy(make_slp_like(N, 30, 40, seed=1700 + i)[0]).cuda()
+           for i, (N, _, _, _) in enumerate(shapes)]  # D = 1,200
+    h = tk.get_handle()
+    try:
+        h.set_option("segment_k", 256)
+        got = _batched(tk, Xds, shapes, "split_bf16", handle=h)
+        ref = [_single(tk, X, L, k, e, "split_bf16") for X, (N, L, k, e) in zip(Xds, shapes)]
+    finally:
+        h.set_option("segment_k", 0)
+    for r, g in zip(ref, got):
+        for a, b in zip(r, g):
+            assert np.array_equal(a, b)

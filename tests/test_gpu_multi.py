@@ -100,3 +100,16 @@ def test_settings_of_different_records_are_refused(tk):
     rc = tk.lib().traknn_knn_scores_multi(tk.get_handle()._h, ctypes.cast(arr, ctypes.c_void_p),
                                           2, 20, None)
     assert rc == 1
+
+
+def test_multi_single_product_bf16(tk):
+    """The single-product BF16 form through the several-settings call agrees with its
+    single calls."""
+    import torch
+    X, _ = make_slp_like(800, 9, 14, seed=47)
+    Xd = torch.from_numpy(X).cuda()
+    got = tk.knn_scores_multi(Xd, SETTINGS[:3], precision="bf16")
+    refs = [tk.knn_scores(Xd, L, k, e, precision="bf16") for L, k, e in SETTINGS[:3]]
+    torch.cuda.synchronize()
+    for (L, k, e), ref, g in zip(SETTINGS[:3], refs, got):
+        _agree(ref, g, k)
