@@ -63,8 +63,9 @@ __device__ __forceinline__ void store_stage(Smem& sm, int buf, int tid, const fl
 }
 
 // G tile rows [r0, r0+128) x columns [c0, c0+128) into sm.G[.][kHalo + .].
-// Each stage's 16 products are summed separately before joining the running
-// sum, which shortens the FP32 accumulation chain 16-fold.
+// Products are summed in partial sums of about sqrt(Dp) terms (whole stages) that
+// then join the running sum: the rounding error of the two FP32 chains grows like
+// sqrt(chain length), and two chains of about sqrt(Dp) terms each keep it smallest.
 __device__ __forceinline__ void gram_tile(Smem& sm, const float* __restrict__ Xc, int N, int Dp,
                                           int r0, int c0, int tid) {
   const int tx = tid & 15, ty = tid >> 4;
@@ -76,6 +77,8 @@ __device__ __forceinline__ void gram_tile(Smem& sm, const float* __restrict__ Xc
 
   float4 ra[2], rb[2];
   const int nk = Dp / BK;
+  const int flush = max(1, (int)(sqrtf((float)Dp) / BK + 0.5f));  // stages per partial sum
+  float part[8][8];
   load_stage(Xc, N, Dp, r0, c0, 0, tid, ra, rb);
   __syncthreads();  // previous users of As/Bs and G are done
   store_stage(sm, 0, tid, ra, rb);
@@ -83,11 +86,12 @@ __device__ __forceinline__ void gram_tile(Smem& sm, const float* __restrict__ Xc
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
     if (kt + 1 < nk) load_stage(Xc, N, Dp, r0, c0, (kt + 1) * BK, tid, ra, rb);
-    float part[8][8];
+    if (kt % flush == 0) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) part[i][j] = 0.f;
+        for (int j = 0; j < 8; ++j) part[i][j] = 0.f;
+    }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       const float4 a0 = *reinterpret_cast<const float4*>(&sm.As[cur][kk][ty * 4]);
@@ -101,10 +105,12 @@ __device__ __forceinline__ void gram_tile(Smem& sm, const float* __restrict__ Xc
 #pragma unroll
         for (int j = 0; j < 8; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
     }
+    if ((kt + 1) % flush == 0 || kt + 1 == nk) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
+        for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
+    }
     if (kt + 1 < nk) store_stage(sm, cur ^ 1, tid, ra, rb);
     __syncthreads();
   }
