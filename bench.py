@@ -315,10 +315,19 @@ def cpu_baseline(X, L, k, e, nrows):
     t0 = time.perf_counter()
     oracle.knn_rows(X, L, k, e, rows)
     el = time.perf_counter() - t0
+    # the small workload in full (all M^2 pairs), for reference
+    from synth import config_inputs
+    Xs, _, cs = config_inputs("small_5y_16x32")
+    Ms = Xs.shape[0] - cs["L"] + 1
+    t1 = time.perf_counter()
+    oracle.knn_scores(Xs, cs["L"], cs["k"], cs["exclusion"])
+    els = time.perf_counter() - t1
     return {"value": nrows * M / el, "unit": "pairs/s", "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": el,
             "sample": f"{nrows} evenly spaced trajectory rows x all M={M} candidates "
-                      f"(FP64 direct differences, full sort)"}
+                      f"(FP64 direct differences, full sort)",
+            "small_full": {"workload": "small_5y_16x32 (N=1826, D=512, L=3, k=10), all pairs",
+                           "seconds": els, "pairs_per_s": float(Ms) * Ms / els}}
 
 
 # ------------------------------------------------------------ extra workloads
