@@ -24,6 +24,9 @@
  *   - Argument errors are detected on the host and returned before anything is
  *     enqueued. Device-side failures (a bounded wait that ran out) are recorded
  *     in the handle and reported by traknn_sync_status().
+ *   - X must hold finite values. NaN or infinite entries make the affected distances
+ *     NaN, which compare false against every bound: their rows' neighbour lists and
+ *     scores are then unspecified (entries may be missing, index -1).
  *   - A handle is not thread-safe: serialise calls that share one handle.
  *     Calls on one handle share its workspace, so two calls on different
  *     streams must not overlap on the GPU.
