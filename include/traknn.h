@@ -225,20 +225,25 @@ traknn_status traknn_knn_stats(traknn_handle handle, const float* nbr_dist, int6
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
  *
  * Its scratch is one fixed 32 MiB array of device memory inside the library,
- * which every GPU that loads the library holds until the process exits. The
- * scratch a problem needs is about
- *     4*N*round_up(D,32) + 260*D + 8*N + 4*M + 8*M*C*k  bytes,  C = min(8, M),
- * plus alignment; larger problems return TRAKNN_ERR_SCRATCH_LIMIT before any
- * work is enqueued. It runs the FP32 CUDA-core path on the current device.
- * Arguments, layouts and outputs are those of traknn_knn_scores (X, nbr_idx,
- * nbr_dist and score are device pointers; `stream` is a cudaStream_t).
+ * which every GPU that loads the library holds until the process exits. A
+ * problem needs exactly
+ *     a(256*D) + a(4*D) + a(8*N) + a(4*M) + a(4*N*Dp) + 2*a(4*M*C*k) + 256  bytes,
+ * with a(x) = x rounded up to a multiple of 256, Dp = D rounded up to a multiple
+ * of 32, and C the number of column chunks: c = min(8, M), C = ceil(M / ceil(M / c)).
+ * Larger problems return TRAKNN_ERR_SCRATCH_LIMIT before any work is enqueued.
+ * It runs the FP32 CUDA-core path on the current device. Arguments, layouts and
+ * outputs are those of traknn_knn_scores (X, nbr_idx, nbr_dist and score are
+ * device pointers; `stream` is a cudaStream_t).
  *
- * The first call on a device looks up the array's device address and caches it,
- * which can also load the library's device code: make that first call before
- * any stream capture. Every call reuses the same array and leaves its contents
- * behind; nothing in it needs to be cleared by the caller. Calls that overlap on
- * the GPU (for example on two streams without an ordering between them) race on
- * the array and corrupt each other's results: serialise them. */
+ * The array's device address is looked up on the first call on a device and
+ * cached for that device's current CUDA context; the lookup can also load the
+ * library's device code, so make the first call before any stream capture. If
+ * the context is destroyed (cudaDeviceReset) and a new one created, the next call
+ * looks the address up again (the array may have moved). Every call reuses the
+ * same array and leaves its contents behind; nothing in it needs to be cleared by
+ * the caller (the call clears its own status word). Calls that overlap on the GPU
+ * (for example on two streams without an ordering between them) race on the array
+ * and corrupt each other's results: serialise them. */
 traknn_status traknn_knn_scores_static(const float* X, int64_t N, int64_t D, int L, int k,
                                        int exclusion, int32_t* nbr_idx, float* nbr_dist,
                                        float* score, void* stream);

@@ -61,6 +61,57 @@ __host__ __device__ inline UnitCoord unit_coord(const Schedule& s, int u) {
   return c;
 }
 
+// Work split of the M x M pair space of the FP32 path (see Schedule above);
+// chunks_opt = 0 takes 8 column chunks (at most 32, at most M).
+inline Schedule make_schedule(int M, int L, int k, int e, int sm_count, int chunks_opt) {
+  Schedule s;
+  s.M = M;
+  s.L = L;
+  s.k = k;
+  s.e = e;
+  s.rows_out = kTileRows - (L - 1);
+  s.strips = (M + s.rows_out - 1) / s.rows_out;
+  int chunks = chunks_opt > 0 ? chunks_opt : 8;
+  chunks = chunks < 32 ? chunks : 32;
+  chunks = chunks < M ? chunks : M;
+  chunks = chunks > 1 ? chunks : 1;
+  s.chunk_cols = (M + chunks - 1) / chunks;
+  s.chunks = (M + s.chunk_cols - 1) / s.chunk_cols;  // every chunk non-empty
+  s.group_strips = sm_count / s.chunks > 1 ? sm_count / s.chunks : 1;
+  const int groups = (s.strips + s.group_strips - 1) / s.group_strips;
+  s.units = groups * s.group_strips * s.chunks;
+  return s;
+}
+
+// Byte offsets of the FP32 path's workspace (each piece starts on a 256-byte
+// boundary): column partial sums, mean, FP64 day norms, window sums, the centred
+// FP32 copy (row pitch Dp = D rounded up to 32) and the partial neighbour lists.
+struct Fp32Layout {
+  size_t partial, mu, norms, W, ops, pd, pi, total;
+  int Dp;
+};
+
+inline Fp32Layout make_layout(int64_t N, int64_t D, const Schedule& s) {
+  Fp32Layout l;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) / 256 * 256;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  l.Dp = (int)((D + 31) / 32 * 32);
+  l.partial = take((size_t)kMeanSlices * D * sizeof(float));
+  l.mu = take((size_t)D * sizeof(float));
+  l.norms = take((size_t)N * sizeof(double));
+  l.W = take((size_t)s.M * sizeof(float));
+  l.ops = take((size_t)N * l.Dp * 4);
+  l.pd = take((size_t)s.M * s.chunks * s.k * sizeof(float));
+  l.pi = take((size_t)s.M * s.chunks * s.k * sizeof(int32_t));
+  l.total = off;
+  return l;
+}
+
 struct FusedArgs {
   Schedule sch;
   int N;              // days

@@ -135,52 +135,6 @@ traknn_status ensure_buffer(traknn_ctx* h, void** buf, size_t* have, size_t need
   return TRAKNN_OK;
 }
 
-// Work split of the M x M pair space of the FP32 path (see Schedule in internal.h).
-Schedule make_schedule(int M, int L, int k, int e, int sm_count, int chunks_opt) {
-  Schedule s;
-  s.M = M;
-  s.L = L;
-  s.k = k;
-  s.e = e;
-  s.rows_out = kTileRows - (L - 1);
-  s.strips = (M + s.rows_out - 1) / s.rows_out;
-  int chunks = chunks_opt > 0 ? chunks_opt : 8;
-  chunks = std::min(chunks, 32);
-  chunks = std::max(1, std::min(chunks, M));
-  s.chunk_cols = (M + chunks - 1) / chunks;
-  s.chunks = (M + s.chunk_cols - 1) / s.chunk_cols;  // every chunk non-empty
-  s.group_strips = std::max(1, sm_count / s.chunks);
-  const int groups = (s.strips + s.group_strips - 1) / s.group_strips;
-  s.units = groups * s.group_strips * s.chunks;
-  return s;
-}
-
-struct Layout {
-  size_t partial, mu, norms, W, ops, pd, pi, total;
-  int Dp;
-};
-
-Layout make_layout(int64_t N, int64_t D, const Schedule& s) {
-  Layout l;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    off = align_up(off, 256);
-    size_t o = off;
-    off += bytes;
-    return o;
-  };
-  l.Dp = (int)align_up((size_t)D, 32);
-  l.partial = take((size_t)kMeanSlices * D * sizeof(float));
-  l.mu = take((size_t)D * sizeof(float));
-  l.norms = take((size_t)N * sizeof(double));
-  l.W = take((size_t)s.M * sizeof(float));
-  l.ops = take((size_t)N * l.Dp * 4);  // centred FP32 copy
-  l.pd = take((size_t)s.M * s.chunks * s.k * sizeof(float));
-  l.pi = take((size_t)s.M * s.chunks * s.k * sizeof(int32_t));
-  l.total = off;
-  return l;
-}
-
 static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 
 // Pitch of the candidate lists: k rounded up to 4 entries, so that every list starts
@@ -734,7 +688,7 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   // plain FP32 CUDA-core path
   const int M = (int)(N - L + 1);
   const Schedule sch = make_schedule(M, L, k, e, h->sm_count, h->col_chunks);
-  const Layout lay = make_layout(N, D, sch);
+  const Fp32Layout lay = make_layout(N, D, sch);
   TRY_ST(ensure_buffer(h, &h->ws, &h->ws_bytes, lay.total));
   char* ws = static_cast<char*>(h->ws);
   float* partial = reinterpret_cast<float*>(ws + lay.partial);

@@ -72,3 +72,39 @@ def check_sampled(X, L, k, e, rows, gidx, gdist, gscore, tol):
     M = X.shape[0] - L + 1
     check_rows(rows, gidx[rows], gdist[rows], gscore[rows], Drows, oidx, odist, oscore, M, k,
                e, tol)
+
+
+def structural_rows(M, L, *, n_random=500, seed=0, strip_every=1, col_bounds=(),
+                    extra=()):
+    """Trajectory rows that exercise the kernels' work split at full size.
+
+    Output rows are cut into strips of 128 - (L-1) rows (one Gram tile height minus
+    the window halo): the first and last row of every `strip_every`-th strip; the
+    rows on both sides of each column boundary in `col_bounds` (work-unit and chunk
+    edges); the first two and last two rows; `extra` rows; and `n_random` seeded
+    random rows."""
+    R = 128 - (L - 1)
+    rows = [0, 1, M - 2, M - 1]
+    for s in range(0, (M + R - 1) // R, strip_every):
+        rows += [s * R, min(M - 1, s * R + R - 1)]
+    for c in col_bounds:
+        rows += [c - 1, c]
+    rows += list(extra)
+    rng = np.random.default_rng(seed)
+    rows += rng.integers(0, M, n_random).tolist()
+    rows = np.unique(np.asarray(rows, dtype=np.int64))
+    return rows[(rows >= 0) & (rows < M)]
+
+
+def tc_unit_bounds(M, L, tiles=8):
+    """Column edges of the tensor-core path's work units (tiles Gram tiles of
+    256 - (L-1) output columns each) and of the tiles inside the first unit."""
+    step = 256 - (L - 1)
+    cols = tiles * step
+    return sorted(set(list(range(cols, M, cols)) + list(range(step, min(M, cols), step))))
+
+
+def fp32_chunk_bounds(M, chunks=8):
+    """Column edges of the FP32 path's column chunks."""
+    cc = -(-M // chunks)
+    return list(range(cc, M, cc))

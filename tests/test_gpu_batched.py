@@ -4,7 +4,7 @@ parity with the FP64 oracle holds series by series."""
 import numpy as np
 import pytest
 
-from parity import check_full
+from parity import check_full, check_sampled, structural_rows, tc_unit_bounds
 from synth import make_slp_like
 
 pytestmark = pytest.mark.gpu
@@ -160,3 +160,31 @@ def test_batched_with_k_segments_equals_single_calls(tk):
     for r, g in zip(ref, got):
         for a, b in zip(r, g):
             assert np.array_equal(a, b)
+
+
+def test_batched_full_grid_series_parity_with_oracle(tk):
+    """Series shaped like the batched workload (1-degree European grid, D = 3,726;
+    N drawn from [3,650, 27,394]; per-series L in 2..10 and k in {5, 10, 20}, exclusion
+    L - 1) in one batched call: every series' sampled rows (boundary rows of every
+    fourth strip, unit edges, 40 random rows) against the oracle, and bitwise
+    equality with the series' own single call for two of them."""
+    import torch
+    rng = np.random.default_rng(20260305)
+    shapes = []
+    for _ in range(7):
+        L = int(rng.integers(2, 11))
+        shapes.append((int(rng.integers(3650, 27395)), L, int(rng.choice([5, 10, 20])), L - 1))
+    shapes.append((27394, 5, 20, 4))  # the longest series of the workload's range
+    Xs = [make_slp_like(N, 46, 81, seed=20260400 + b)[0] for b, (N, _, _, _) in enumerate(shapes)]
+    Xds = [torch.from_numpy(X).cuda() for X in Xs]
+    got = _batched(tk, Xds, shapes, "split_bf16")
+    for b, (X, (N, L, k, e), (idx, dist, score)) in enumerate(zip(Xs, shapes, got)):
+        M = N - L + 1
+        rows = structural_rows(M, L, n_random=40, seed=b, strip_every=4,
+                               col_bounds=tc_unit_bounds(M, L)[::3])
+        check_sampled(X, L, k, e, rows, idx, dist, score, 2e-4)
+    for b in (0, len(shapes) - 1):
+        N, L, k, e = shapes[b]
+        ref = _single(tk, Xds[b], L, k, e, "split_bf16")
+        for x, y in zip(ref, got[b]):
+            assert np.array_equal(x, y), shapes[b]

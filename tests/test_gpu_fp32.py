@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from conftest import load_golden
-from parity import check_full, check_sampled
+from parity import check_full, check_sampled, fp32_chunk_bounds, structural_rows
 from synth import config_inputs, make_slp_like
 
 pytestmark = pytest.mark.gpu
@@ -80,9 +80,11 @@ def test_euro_75y_sampled_rows(tk):
     L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
     idx, dist, score = _run(tk, X, L, k, e)
     M = X.shape[0] - L + 1
-    rng = np.random.default_rng(0)
-    rows = np.unique(np.concatenate([[0, 1, 123, 124, M - 2, M - 1], meta.planted_starts,
-                                     rng.integers(0, M, 10)]))
+    # first and last row of every strip, the column-chunk edges, the planted
+    # anomalies and 500 seeded random rows
+    rows = structural_rows(M, L, n_random=500, seed=0, col_bounds=fp32_chunk_bounds(M),
+                           extra=meta.planted_starts)
+    assert len(rows) >= 900
     check_sampled(X, L, k, e, rows, idx, dist, score, TOL)
     # the planted multi-day anomalies are the rarest trajectories
     order = np.argsort(-score)
