@@ -583,8 +583,52 @@ def suite_ext(args):
             "small_D": {"workload": f"N={N}, D=32 (4x8), L={L}, k={k}", **small}}
 
 
+def suite_smalld(args):
+    """Small grids (a stand-in for fields reduced to a few dozen principal components,
+    Sec. 5): 75 years of D-value fields for D = 32 ... 512, L = 5, k = 20, with
+    trajectory-embedded operands and with diagonal window sums. At small D the fused
+    kernel's epilogue, not the contraction, sets the time; its bound is the CUDA-core
+    work of the scan per output (about 8 FP32 operations: correction FMA, distance FMA,
+    clamp, two compares, mask bits), reported against the FP32 ALU peak."""
+    import torch
+
+    import paper_2603_02059_gb300 as tk
+    from synth import make_slp_like
+    h = tk.get_handle()
+    peaks, src = measured_peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    alu_peak = fp32_alu_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
+    out = []
+    N, L, k, e = 27394, 5, 20, 4
+    M = N - L + 1
+    for gh, gw in ((4, 8), (8, 8), (8, 16), (16, 16), (16, 32)):
+        X, _ = make_slp_like(N, gh, gw, seed=20260310, annual_amp=5.0)
+        Xd = torch.from_numpy(X).cuda()
+        row = {"D": gh * gw}
+        for embed in ("always", "never"):
+            h.profile_read()
+            h.set_option("profile", 1)
+            ms = _events_ms(lambda: tk.knn_scores(Xd, L, k, e, embed=embed, handle=h),
+                            args.steps, 3)
+            kms = h.profile_read()[3:]
+            h.set_option("profile", 0)
+            kavg = statistics.mean(kms) if kms else None
+            # one evaluated output per unordered pair: M(M+1)/2 outputs
+            ops = 8.0 * M * (M + 1) / 2
+            row[embed] = {"ms_per_step": ms, "pairs_per_s": float(M) * M / (ms * 1e-3),
+                          "kernel_ms": kavg,
+                          "epilogue_alu_frac": (ops / (kavg * 1e-3) / 1e12 / alu_peak)
+                          if kavg else None}
+        out.append(row)
+        del Xd
+    if h.sync_status() != 0:
+        raise RuntimeError("device-side failure")
+    return {"suite": "smalld", "workload": f"N={N}, L={L}, k={k}, exclusion={e}",
+            "sweep": out, "alu_peak_tflops": alu_peak, "peak_source": src}
+
+
 SUITES = {"precision": suite_precision, "batched": suite_batched, "adjoint": suite_adjoint,
-          "ext": suite_ext}
+          "ext": suite_ext, "smalld": suite_smalld}
 
 
 # --------------------------------------------------------------- reference arm

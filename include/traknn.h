@@ -91,9 +91,15 @@ typedef enum {
                                         accumulation over large D (0 = default 8192) */
   TRAKNN_OPT_GROUP_STRIPS = 11,      /* tensor-core paths: row strips whose work units are handed
                                         out side by side (sharing operand tiles in L2; 0 = 19) */
-  TRAKNN_OPT_L2_KEEP_A = 12          /* tensor-core paths: 1 loads a unit's row-strip operand with
+  TRAKNN_OPT_L2_KEEP_A = 12,         /* tensor-core paths: 1 loads a unit's row-strip operand with
                                         an L2 evict-last policy (it is re-read for every tile of
                                         the unit; default 0) */
+  TRAKNN_OPT_EMBED = 13              /* tensor-core traknn_knn_scores with L > 1: 1 builds one
+                                        operand row per trajectory (its L days, Eq. 1, L*D values)
+                                        so that one Gram entry is the whole window sum of Eq. 2
+                                        (L times the contraction, no diagonal sums); 2 never;
+                                        0 (default) when L*D <= 1024, the small-grid form (Sec. 5:
+                                        fields reduced to a few dozen principal components) */
 } traknn_option;
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */

@@ -23,10 +23,11 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_AL
           4: "ERR_CUDA", 5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED_DEVICE", 7: "ERR_UNSUPPORTED",
           8: "ERR_SCRATCH_LIMIT"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
+EMBED = {"auto": 0, "always": 1, "never": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
           "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7, "stats": 8,
           "autotune": 9, "segment_k": 10,
-          "group_strips": 11, "l2_keep_a": 12}
+          "group_strips": 11, "l2_keep_a": 12, "embed": 13}
 
 
 class Series(ctypes.Structure):
@@ -128,7 +129,7 @@ class Handle:
         _check(lib().traknn_set_option(self._h, OPTION[name], int(value)), f"set_option({name})")
 
     def configure(self, precision=None, center=None, col_chunks=None, symmetric=None,
-                  unit_cols=None, autotune=None):
+                  unit_cols=None, autotune=None, embed=None):
         if precision is not None:
             self.set_option("precision", PRECISION[precision])
         if center is not None:
@@ -141,6 +142,8 @@ class Handle:
             self.set_option("unit_cols", int(unit_cols))
         if autotune is not None:
             self.set_option("autotune", int(autotune))
+        if embed is not None:
+            self.set_option("embed", EMBED[embed])
 
     def set_grid_weights(self, w):
         """Grid-point weights for later calls (a [D] float32 CUDA tensor kept alive by
@@ -203,18 +206,20 @@ def _as_input(X: torch.Tensor) -> torch.Tensor:
 
 def knn_scores(X: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
                precision: str = "split_bf16", center: bool = True, col_chunks: int = 0,
-               symmetric: bool = True, unit_cols: int = 0, handle: Handle | None = None,
-               out=None):
+               symmetric: bool = True, unit_cols: int = 0, embed: str = "auto",
+               handle: Handle | None = None, out=None):
     """Neighbour indices [M, k] int32, distances [M, k] float32 and rarity scores [M]
     float32 for every L-day trajectory of X (M = N - L + 1). `exclusion` defaults to
-    L - 1 (overlapping trajectories are not candidates)."""
+    L - 1 (overlapping trajectories are not candidates). `embed` ("auto", "always",
+    "never") selects trajectory-embedded operands on the tensor cores
+    (TRAKNN_OPT_EMBED)."""
     X = _as_input(X)
     N, D = X.shape
     e = L - 1 if exclusion is None else int(exclusion)
     M = N - L + 1
     h = handle or get_handle(X.device.index)
     h.configure(precision=precision, center=center, col_chunks=col_chunks, symmetric=symmetric,
-                unit_cols=unit_cols)
+                unit_cols=unit_cols, embed=embed)
     if out is None:
         idx = torch.empty((max(M, 0), k), dtype=torch.int32, device=X.device)
         dist = torch.empty((max(M, 0), k), dtype=torch.float32, device=X.device)
@@ -321,8 +326,8 @@ def knn_stats(dist: torch.Tensor, k_id: int | None = None, *, prefix: bool = Tru
 
 def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
                     precision: str = "split_bf16", center: bool = True, col_chunks: int = 0,
-                    symmetric: bool = True, unit_cols: int = 0, handle=None, out=None,
-                    device: int | None = None):
+                    symmetric: bool = True, unit_cols: int = 0, embed: str = "auto",
+                    handle=None, out=None, device: int | None = None):
     """Host-buffer variant: X_host is a CPU float32 tensor (pinned for fast copies);
     returns CPU tensors. The call copies in, computes, copies out and synchronises."""
     if X_host.is_cuda or X_host.dtype != torch.float32 or X_host.dim() != 2:
@@ -333,7 +338,7 @@ def knn_scores_host(X_host: torch.Tensor, L: int, k: int, exclusion: int | None 
     M = N - L + 1
     h = handle or get_handle(device)
     h.configure(precision=precision, center=center, col_chunks=col_chunks, symmetric=symmetric,
-                unit_cols=unit_cols)
+                unit_cols=unit_cols, embed=embed)
     if out is None:
         pin = X_host.is_pinned()
         idx = torch.empty((M, k), dtype=torch.int32, pin_memory=pin)

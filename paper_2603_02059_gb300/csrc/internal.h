@@ -250,7 +250,9 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
 // Operand layout of the tensor-core path: groups = ceil(D / 63) groups of 64 K
 // entries (63 permuted grid points + 1 correction entry); pitch groups * 64.
 inline int tc_groups(int D) { return (D + 62) / 63; }
-cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int groups,
+// emb > 1: each operand row is the emb-day trajectory starting at that day (emb * D
+// values, contiguous in X); the series table then describes trajectories (N = M, L = 1).
+cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int emb, int groups,
                                      bool correct, const float* mu, const float* wts, void* hi,
                                      void* lo, double* norms, float* cval, cudaStream_t st);
 cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
@@ -258,8 +260,8 @@ cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const doub
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
                          cudaStream_t st);
 // Adjoint of the summed weighted score (kernels_adjoint.cu); `ws` must hold
-// adjoint_workspace_bytes(M, k) bytes. Adds the number of launches to *launches.
-size_t adjoint_workspace_bytes(int M, int k);
+// adjoint_workspace_bytes(N, L, k) bytes. Adds the number of launches to *launches.
+size_t adjoint_workspace_bytes(int N, int L, int k);
 // wts: optional [D] grid-point weights (dX is multiplied by w_p), or null.
 cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int32_t* idx,
                            const float* g, const float* wts, float* dX, void* ws, int* err,

@@ -629,19 +629,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (ch > 0)
             for (int c = 0; c < L - 1; ++c) grow[c] = grow[32 + c];
           const float* cs = Csh + ch * 32;
+          // Gram values of the chunk (correction added back): staged in shared memory
+          // for the diagonal window sums, or, with L = 1 (no window), kept in registers
+          float c[32];
           if (nseg == 1) {
             ptx::tmem_wait();
 #pragma unroll
-            for (int x = 0; x < 32; ++x)
-              grow[(L - 1) + x] = fmaf(crow, cs[x], __uint_as_float(vr[x]));
+            for (int x = 0; x < 32; ++x) c[x] = fmaf(crow, cs[x], __uint_as_float(vr[x]));
           } else {
             uint32_t tv[32];
             ptx::tmem_ld32_async(tlast + (uint32_t)(ch * 32), tv);
             ptx::tmem_wait();
 #pragma unroll
             for (int x = 0; x < 32; ++x)
-              grow[(L - 1) + x] =
-                  fmaf(crow, cs[x], __uint_as_float(vr[x]) + __uint_as_float(tv[x]));
+              c[x] = fmaf(crow, cs[x], __uint_as_float(vr[x]) + __uint_as_float(tv[x]));
+          }
+          if (L > 1) {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) grow[(L - 1) + x] = c[x];
           }
           if (kAhead && ch + 1 < BN / 32) {
             if (nseg == 1)
@@ -656,7 +661,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             released = true;
           }
           lap(2);
-          ptx::named_bar_sync(bar, kEpiThreads);
+          // the window sums read other rows' staged values (nothing to wait for at L = 1)
+          if (L > 1) ptx::named_bar_sync(bar, kEpiThreads);
           lap(3);
           const int j0 = c0 + ch * 32 - (L - 1);
           // column side of this chunk: output columns j >= jsym inside the unit
@@ -664,7 +670,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                 bit_range(ch == 0 ? L - 1 : 0, 32)
                                           : 0u;
           uint32_t cand = 0, ccand = 0;
-          float c[32];
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
             // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
@@ -674,12 +679,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* g0 = Gbuf + l * LDG;
             const float* wv = Wsh + ch * 32;
             const float* tv = Tsh + ch * 32;
+            if (L > 1) {
 #pragma unroll
-            for (int x = 0; x < 32; ++x) c[x] = g0[x];
-            for (int m = 1; m < L; ++m) {
-              const float* gm = g0 + m * (LDG + 1);
+              for (int x = 0; x < 32; ++x) c[x] = g0[x];
+              for (int m = 1; m < L; ++m) {
+                const float* gm = g0 + m * (LDG + 1);
 #pragma unroll
-              for (int x = 0; x < 32; ++x) c[x] += gm[x];
+                for (int x = 0; x < 32; ++x) c[x] += gm[x];
+              }
             }
             const float lthr = list.threshold();
 #pragma unroll

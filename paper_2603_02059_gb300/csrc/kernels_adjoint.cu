@@ -8,10 +8,22 @@
 //   reverse:  j in [a-L+1, a], t with j in N_t,       b = t + (a - j)
 // With grid-point weights w_p (distance sum_p w_p (x_p - y_p)^2) every term carries
 // the factor w_p, applied once to the finished sum.
-// Each output row is owned by one CTA that sums its incidences in a fixed order,
-// so no floating-point atomics are used and the result is bitwise reproducible.
-// The reverse lists (who has j as a neighbour) come from a counting sort whose
-// segments are then sorted by t (heap sort, one thread per segment).
+//
+// Neighbouring trajectories have neighbouring neighbours (j in N_t makes j+1 in
+// N_{t+1} likely), so the incidences of a run of consecutive days share many partner
+// rows. The gradient is therefore taken per block of kAdjR consecutive days:
+//   build:  the block's incidences are listed in shared memory as keys (partner b,
+//           day in block, kind, window slot), sorted, and every run with the same
+//           (b, day) is merged into one entry (b, day, summed weight);
+//   gather: one CTA per (day block, 256 grid points) applies the block's entries in
+//           list order, so that every partner row segment is read once per block,
+//           and all CTAs of one 256-point tile run first (that tile of X, 1 KB per
+//           day, stays in L2 while it is re-read).
+// No floating-point atomics are used: every sum is taken in a fixed order (sorted
+// keys, then list order), so the result is bitwise reproducible. A single day with
+// more incidences than the sort buffer lists them unmerged in a fixed order (its
+// forward incidences by (t, rank), then its reverse ones by (j, t), from reverse
+// lists sorted by t).
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -79,7 +91,19 @@ __device__ void sift_down(int* a, int root, int n) {
   }
 }
 
-constexpr int kMaxInc = 2048;  // incidences of one day merged in the gather's shared memory
+constexpr int kAdjR = 32;         // output days per block
+constexpr int kKeyCap = 4096;     // incidences sorted at once in shared memory
+constexpr int kBuildThreads = 256;
+constexpr int kGatherCols = 256;  // grid points per gather CTA (one per thread)
+
+// One merged entry of a block's gradient list: partner day b, output day a0 + d,
+// summed weight w (16 bytes, read as one vector).
+struct AdjEntry {
+  int b;
+  int d;
+  float w;
+  int pad;
+};
 
 // Incidences of day a: the forward ones (k per trajectory t of its window) and the
 // reverse segments of the days j of its window, [max(0, a-L+1), min(a, M-1)].
@@ -89,16 +113,16 @@ __device__ __forceinline__ int day_incidences(const int* off, int a, int L, int 
   return (t_hi - t_lo + 1) * k + (off[t_hi + 1] - off[t_lo]);
 }
 
-// Sort ascending (heap sort, in place) every reverse segment that some day reads one
-// incidence at a time: a day with more incidences than the gather's buffer, whose
-// summation order must not depend on the order the fill kernel produced. The other
-// days order their incidences by key in the gather and need no sorted segments.
+// Sort ascending (heap sort, in place) every reverse segment read by a day with more
+// incidences than the sort buffer holds; that day lists its incidences unmerged, in
+// an order that must not depend on the order the fill kernel produced. Other days
+// order their incidences by key in the build kernel and need no sorted segments.
 __global__ void adj_sort_kernel(const int* __restrict__ off, int N, int L, int M, int k,
                                 int* rev) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   bool needed = false;
-  for (int d = j; d < min(N, j + L); ++d) needed |= day_incidences(off, d, L, M, k) > kMaxInc;
+  for (int d = j; d < min(N, j + L); ++d) needed |= day_incidences(off, d, L, M, k) > kKeyCap;
   if (!needed) return;
   int* a = rev + off[j];
   const int n = off[j + 1] - off[j];
@@ -111,75 +135,126 @@ __global__ void adj_sort_kernel(const int* __restrict__ off, int N, int L, int M
   }
 }
 
-constexpr int kGatherThreads = 256;
-constexpr int kPerThread = kMaxInc / kGatherThreads;  // consecutive positions per thread
-
-// One CTA per day a: dX[a] = sum over incidences w (X[a] - X[b]).
-//
-// The incidences are listed in shared memory as keys (partner day b, kind, window
-// slot): a forward incidence (trajectory t, neighbour j, b = j + a - t) has kind 0
-// and slot t - t_lo, a reverse one (j in the window, t with j among its neighbours,
-// b = t + a - j) kind 1 and slot j - t_lo. For one partner no two incidences share
-// kind and slot, so the sorted order does not depend on the order the lists were
-// built in. The weights of each partner are summed in key order and the partners
-// are visited in increasing day order, so every partner row X[b] is read once
-// (consecutive days tend to have consecutive neighbours, so a day's incidences have
-// about half as many distinct partners). A day with more incidences than the buffer
-// holds sums them one by one, forward then reverse in sorted segments. Both ways the
-// order is fixed, so the result is bitwise reproducible.
-__global__ void __launch_bounds__(kGatherThreads)
-    adj_gather_kernel(const float* __restrict__ X, int N, int D, int L, int M, int k,
-                      const int32_t* __restrict__ idx, const float* __restrict__ g,
-                      const int* __restrict__ off, const int* __restrict__ rev,
-                      const float* __restrict__ wts, float* __restrict__ dX) {
-  __shared__ unsigned long long key[kMaxInc];  // (partner << 32) | position
-  __shared__ float wsum[kMaxInc];              // merged weight of each distinct partner
-  __shared__ int part[kMaxInc];                // distinct partners, increasing
-  __shared__ int scan[kGatherThreads];
-  __shared__ int rstart[kMaxL + 1];            // first position of each reverse segment
-  const int a = blockIdx.x;
+// Exclusive scan of the blocks' incidence totals (upper bounds of their entry counts)
+// into blk_off[0..nblk]; one block of 1024 threads.
+__global__ void adj_block_scan_kernel(const int* __restrict__ off, int N, int L, int M, int k,
+                                      int nblk, long long* blk_off) {
+  __shared__ long long part[1024];
   const int tid = threadIdx.x;
-  const float* xa = X + (size_t)a * D;
-  const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
-  const int nt = max(0, t_hi - t_lo + 1);
+  const int per = (nblk + 1023) / 1024;
+  const int lo = min(nblk, tid * per), hi = min(nblk, lo + per);
+  auto total = [&](int blk) {
+    long long s = 0;
+    for (int a = blk * kAdjR; a < min(N, (blk + 1) * kAdjR); ++a)
+      s += day_incidences(off, a, L, M, k);
+    return s;
+  };
+  long long s = 0;
+  for (int i = lo; i < hi; ++i) s += total(i);
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const long long v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long run = tid > 0 ? part[tid - 1] : 0;
+  for (int i = lo; i < hi; ++i) {
+    blk_off[i] = run;
+    run += total(i);
+  }
+  if (tid == 1023) blk_off[nblk] = part[1023];
+}
+
+// The merged entry list of one block of kAdjR days (one CTA per block). The days are
+// cut into segments of consecutive days whose incidences fit the key buffer. A
+// segment's keys are (partner b << 32) | (day d << 24) | (kind << 23) | slot: kind 0 is
+// a forward incidence (trajectory t = t_lo + slot of day a0 + d), kind 1 a reverse one
+// (window day j = t_lo + slot, trajectory t = b - a + j). Every key is unique, so the
+// sorted order is fixed whatever order the reverse lists were filled in; each run of
+// equal (b, d) becomes one entry whose weight is summed in key order.
+__global__ void __launch_bounds__(kBuildThreads)
+    adj_build_kernel(const int32_t* __restrict__ idx, const float* __restrict__ g, int N, int L,
+                     int M, int k, const int* __restrict__ off, const int* __restrict__ rev,
+                     const long long* __restrict__ blk_off, int* __restrict__ blk_nnz,
+                     AdjEntry* __restrict__ ent) {
+  __shared__ unsigned long long key[kKeyCap];
+  __shared__ int dayoff[kAdjR + 1];  // first position of each day in the block
+  __shared__ int scan[kBuildThreads];
+  const int tid = threadIdx.x;
+  const int a0 = blockIdx.x * kAdjR;
+  const int nd = min(kAdjR, N - a0);
   const float inv_k2 = 2.0f / (float)k;
-  const int nfwd = nt * k;
   if (tid == 0) {
-    int pos = nfwd;
-    for (int j = t_lo; j <= t_hi; ++j) {
-      rstart[j - t_lo] = pos;
-      pos += off[j + 1] - off[j];
+    int pos = 0;
+    for (int d = 0; d < nd; ++d) {
+      dayoff[d] = pos;
+      pos += day_incidences(off, a0 + d, L, M, k);
     }
-    rstart[nt] = pos;
+    dayoff[nd] = pos;
   }
   __syncthreads();
-  const int ninc = rstart[nt];
-  const bool merged = ninc <= kMaxInc;
-  int nu = 0;
-  if (merged) {
+  AdjEntry* out = ent + blk_off[blockIdx.x];
+  int nout = 0;
+  // incidence q (0 <= q < day_incidences) of day a: its partner and trajectory
+  auto incidence = [&](int a, int q, int& b, int& t, int& kind, int& slot) -> bool {
+    const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
+    const int nfwd = (t_hi - t_lo + 1) * k;
+    if (q < nfwd) {
+      slot = q / k;
+      t = t_lo + slot;
+      kind = 0;
+      const int j = idx[(size_t)t * k + q % k];
+      b = j + a - t;
+      return j >= 0 && j < M;
+    }
+    const int r = off[t_lo] + (q - nfwd);  // reverse lists of t_lo..t_hi are contiguous
+    int j = t_lo;
+    while (off[j + 1] <= r) ++j;
+    t = rev[r];
+    kind = 1;
+    slot = j - t_lo;
+    b = t + a - j;
+    return true;
+  };
+  int d = 0;
+  while (d < nd) {
+    int dh = d + 1;
+    while (dh < nd && dayoff[dh + 1] - dayoff[d] <= kKeyCap) ++dh;
+    const int base = dayoff[d];
+    const int n = dayoff[dh] - base;
+    if (n > kKeyCap) {
+      // one day with more incidences than the buffer: unmerged, in the fixed order of
+      // its lists (forward by (t, rank), reverse by (j, t) from sorted segments)
+      const int a = a0 + d;
+      for (int q = tid; q < n; q += kBuildThreads) {
+        int b, t, kind, slot;
+        const bool ok = incidence(a, q, b, t, kind, slot);
+        out[nout + q] = ok ? AdjEntry{b, d, inv_k2 * g[t], 0} : AdjEntry{a, d, 0.f, 0};
+      }
+      nout += n;
+      d = dh;
+      continue;
+    }
     int n2 = 1;
-    while (n2 < ninc) n2 <<= 1;
-    for (int q = tid; q < n2; q += kGatherThreads) {
-      unsigned long long kq = ~0ull;  // padding and invalid entries sort last
-      if (q < nfwd) {
-        const int ts = q / k;
-        const int t = t_lo + ts;
-        const int j = idx[(size_t)t * k + q % k];
-        if (j >= 0 && j < M) kq = ((unsigned long long)(unsigned)(j + a - t) << 32) | (unsigned)ts;
-      } else if (q < ninc) {
-        int sg = 0;
-        while (rstart[sg + 1] <= q) ++sg;  // reverse segment of day j = t_lo + sg
-        const int j = t_lo + sg;
-        const int t = rev[off[j] + (q - rstart[sg])];
-        kq = ((unsigned long long)(unsigned)(t + a - j) << 32) | (1u << 16) | (unsigned)sg;
+    while (n2 < n) n2 <<= 1;
+    for (int q = tid; q < n2; q += kBuildThreads) {
+      unsigned long long kq = ~0ull;  // padding and invalid incidences sort last
+      if (q < n) {
+        int dd = d;
+        while (dayoff[dd + 1] <= base + q) ++dd;
+        int b, t, kind, slot;
+        if (incidence(a0 + dd, base + q - dayoff[dd], b, t, kind, slot))
+          kq = ((unsigned long long)(unsigned)b << 32) | ((unsigned long long)dd << 24) |
+               ((unsigned long long)kind << 23) | (unsigned long long)slot;
       }
       key[q] = kq;
     }
     __syncthreads();
-    // bitonic sort of the n2 keys (ascending)
     for (int size = 2; size <= n2; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int q = tid; q < n2; q += kGatherThreads) {
+        for (int q = tid; q < n2; q += kBuildThreads) {
           const int r = q ^ stride;
           if (r > q) {
             const bool up = (q & size) == 0;
@@ -193,110 +268,149 @@ __global__ void __launch_bounds__(kGatherThreads)
         __syncthreads();
       }
     }
-    // run heads (first position of each distinct valid partner), numbered by an
-    // exclusive prefix sum over the thread's kPerThread consecutive positions
+    // run heads (first position of each distinct (b, day)), numbered by an exclusive
+    // prefix sum over each thread's consecutive positions
+    const int per = (n + kBuildThreads - 1) / kBuildThreads;
     auto head = [&](int q) {
-      if (q >= ninc || key[q] == ~0ull) return 0;
-      return (q == 0 || (key[q - 1] >> 32) != (key[q] >> 32)) ? 1 : 0;
+      if (q >= n || key[q] == ~0ull) return 0;
+      return (q == 0 || (key[q - 1] >> 24) != (key[q] >> 24)) ? 1 : 0;
     };
-    const int q0 = tid * kPerThread;
+    const int q0 = tid * per;
     int cnt = 0;
-    for (int i = 0; i < kPerThread; ++i) cnt += head(q0 + i);
+    for (int i = 0; i < per; ++i) cnt += head(q0 + i);
     scan[tid] = cnt;
     __syncthreads();
-    for (int o = 1; o < kGatherThreads; o <<= 1) {
+    for (int o = 1; o < kBuildThreads; o <<= 1) {
       const int v = tid >= o ? scan[tid - o] : 0;
       __syncthreads();
       scan[tid] += v;
       __syncthreads();
     }
-    int u = scan[tid] - cnt;
-    for (int i = 0; i < kPerThread; ++i) {
+    int u = nout + scan[tid] - cnt;
+    for (int i = 0; i < per; ++i) {
       const int q = q0 + i;
       if (!head(q)) continue;
-      const unsigned long long b = key[q] >> 32;
+      const unsigned long long run = key[q] >> 24;
+      const int b = (int)(key[q] >> 32);
+      const int dd = (int)((key[q] >> 24) & 0xFF);
+      const int a = a0 + dd;
+      const int t_lo = max(0, a - L + 1);
       float w = 0.f;
-      for (int r = q; r < ninc && key[r] != ~0ull && (key[r] >> 32) == b; ++r) {
-        // the incidence's trajectory t, recovered from its kind and slot
-        const unsigned lo = (unsigned)key[r];
-        const int slot = (int)(lo & 0xFFFFu);
-        const int t = (lo >> 16) ? (int)b - a + t_lo + slot : t_lo + slot;
+      for (int r = q; r < n && key[r] != ~0ull && (key[r] >> 24) == run; ++r) {
+        const int kind = (int)((key[r] >> 23) & 1);
+        const int slot = (int)(key[r] & 0x7F);
+        const int t = kind ? b - a + t_lo + slot : t_lo + slot;
         w += inv_k2 * g[t];
       }
-      part[u] = (int)b;
-      wsum[u] = w;
-      ++u;
+      out[u++] = AdjEntry{b, dd, w, 0};
     }
-    nu = scan[kGatherThreads - 1];
-    __syncthreads();
+    nout += scan[kBuildThreads - 1];
+    __syncthreads();  // the key buffer is refilled by the next segment
+    d = dh;
   }
-  for (int p0 = 0; p0 < D; p0 += kGatherThreads * 4) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    float xv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int p = p0 + u * kGatherThreads + tid;
-      xv[u] = p < D ? xa[p] : 0.f;
+  if (tid == 0) blk_nnz[blockIdx.x] = nout;
+}
+
+// dX for one block of kAdjR days and kGatherCols grid points: every entry (b, d, w) of
+// the block's list adds w (X[a0+d] - X[b]) to day a0 + d, in list order. Each thread
+// owns one grid point, so its rows of X[a0 ..] and of the sums live in shared memory
+// columns that no other thread touches. blockIdx.x is the day block and blockIdx.y
+// the grid-point tile: CTAs are scheduled with x fastest, so the CTAs running at one
+// time share a tile of X, which stays in L2 while the entries re-read its rows.
+__global__ void __launch_bounds__(kGatherCols)
+    adj_gather_kernel(const float* __restrict__ X, int N, int D,
+                      const long long* __restrict__ blk_off, const int* __restrict__ blk_nnz,
+                      const AdjEntry* __restrict__ ent, const float* __restrict__ wts,
+                      float* __restrict__ dX) {
+  extern __shared__ float adj_sm[];
+  float(*xa)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm);
+  float(*acc)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm + kAdjR * kGatherCols);
+  const int tid = threadIdx.x;
+  const int a0 = blockIdx.x * kAdjR;
+  const int nd = min(kAdjR, N - a0);
+  const int4* e4 = reinterpret_cast<const int4*>(ent + blk_off[blockIdx.x]);
+  const int n = blk_nnz[blockIdx.x];
+  const int tiles = (D + kGatherCols - 1) / kGatherCols;
+  for (int tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
+    const int p = tile * kGatherCols + tid;
+    const bool pin = p < D;
+#pragma unroll 4
+    for (int d = 0; d < kAdjR; ++d) {
+      xa[d][tid] = (pin && d < nd) ? __ldg(X + (size_t)(a0 + d) * D + p) : 0.f;
+      acc[d][tid] = 0.f;
     }
-    if (merged) {
-      for (int v = 0; v < nu; ++v) {
-        const float w = wsum[v];
-        const float* xb = X + (size_t)part[v] * D;
+    const float* xp = X + (pin ? p : 0);
+    constexpr int U = 8;  // entries whose partner values are loaded together
+    int q = 0;
+    for (; q + U <= n; q += U) {
+      int4 e[U];
+      float xb[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int p = p0 + u * kGatherThreads + tid;
-          if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
-        }
-      }
-    } else {
-      for (int t = t_lo; t <= t_hi; ++t) {
-        const float w = inv_k2 * g[t];
-        for (int i = 0; i < k; ++i) {
-          const int j = idx[(size_t)t * k + i];
-          if (j < 0 || j >= M) continue;
-          const float* xb = X + (size_t)(j + a - t) * D;
+      for (int u = 0; u < U; ++u) e[u] = __ldg(e4 + q + u);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int p = p0 + u * kGatherThreads + tid;
-            if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
-          }
-        }
-      }
-      for (int j = t_lo; j <= t_hi; ++j) {
-        for (int r = off[j]; r < off[j + 1]; ++r) {
-          const int t = rev[r];
-          const float w = inv_k2 * g[t];
-          const float* xb = X + (size_t)(t + a - j) * D;
+      for (int u = 0; u < U; ++u) xb[u] = pin ? __ldg(xp + (size_t)e[u].x * D) : 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int p = p0 + u * kGatherThreads + tid;
-            if (p < D) acc[u] = fmaf(w, xv[u] - xb[p], acc[u]);
-          }
-        }
+      for (int u = 0; u < U; ++u) {
+        const int d = e[u].y;
+        acc[d][tid] = fmaf(__int_as_float(e[u].z), xa[d][tid] - xb[u], acc[d][tid]);
       }
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int p = p0 + u * kGatherThreads + tid;
-      if (p < D) dX[(size_t)a * D + p] = wts ? acc[u] * wts[p] : acc[u];
+    for (; q < n; ++q) {
+      const int4 e = __ldg(e4 + q);
+      const float xb = pin ? __ldg(xp + (size_t)e.x * D) : 0.f;
+      acc[e.y][tid] = fmaf(__int_as_float(e.z), xa[e.y][tid] - xb, acc[e.y][tid]);
+    }
+    if (pin) {
+      const float wp = wts ? wts[p] : 1.f;
+#pragma unroll 4
+      for (int d = 0; d < nd; ++d)
+        dX[(size_t)(a0 + d) * D + p] = wts ? acc[d][tid] * wp : acc[d][tid];
     }
   }
 }
 
 }  // namespace
 
-size_t adjoint_workspace_bytes(int M, int k) {
-  return ((size_t)3 * M + 1 + (size_t)M * k) * sizeof(int) + 1024;
+namespace {
+
+inline size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Workspace layout: merged entries (at most one per incidence, 2 L k M in all), block
+// offsets and counts, then the reverse neighbour index (count, cursor, off, rev).
+struct AdjLayout {
+  size_t ent, blk_off, blk_nnz, count, total;
+};
+
+AdjLayout adj_layout(int N, int L, int k) {
+  const size_t M = (size_t)(N - L + 1);
+  const size_t nblk = ((size_t)N + kAdjR - 1) / kAdjR;
+  AdjLayout l;
+  l.ent = 0;
+  l.blk_off = up256(2 * (size_t)L * k * M * sizeof(AdjEntry));
+  l.blk_nnz = l.blk_off + up256((nblk + 1) * sizeof(long long));
+  l.count = l.blk_nnz + up256(nblk * sizeof(int));
+  l.total = l.count + up256((3 * M + 1 + M * (size_t)k) * sizeof(int));
+  return l;
 }
+
+}  // namespace
+
+size_t adjoint_workspace_bytes(int N, int L, int k) { return adj_layout(N, L, k).total; }
 
 cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int32_t* idx,
                            const float* g, const float* wts, float* dX, void* ws, int* err,
                            cudaStream_t st, int* launches) {
   const int M = N - L + 1;
-  int* count = static_cast<int*>(ws);
+  const AdjLayout lay = adj_layout(N, L, k);
+  char* base = static_cast<char*>(ws);
+  AdjEntry* ent = reinterpret_cast<AdjEntry*>(base + lay.ent);
+  long long* blk_off = reinterpret_cast<long long*>(base + lay.blk_off);
+  int* blk_nnz = reinterpret_cast<int*>(base + lay.blk_nnz);
+  int* count = reinterpret_cast<int*>(base + lay.count);
   int* cursor = count + M;
   int* off = cursor + M;
   int* rev = off + M + 1;
+  const int nblk = (N + kAdjR - 1) / kAdjR;
   cudaError_t e = cudaMemsetAsync(count, 0, (size_t)2 * M * sizeof(int), st);
   if (e != cudaSuccess) return e;
   const long long nq = (long long)M * k;
@@ -305,8 +419,17 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_scan_kernel<<<1, 1024, 0, st>>>(count, M, off);
   adj_fill_kernel<<<blocks, 256, 0, st>>>(idx, M, k, off, cursor, rev);
   adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, N, L, M, k, rev);
-  adj_gather_kernel<<<N, kGatherThreads, 0, st>>>(X, N, D, L, M, k, idx, g, off, rev, wts, dX);
-  *launches += 5;
+  adj_block_scan_kernel<<<1, 1024, 0, st>>>(off, N, L, M, k, nblk, blk_off);
+  adj_build_kernel<<<nblk, kBuildThreads, 0, st>>>(idx, g, N, L, M, k, off, rev, blk_off,
+                                                    blk_nnz, ent);
+  const size_t smem = 2 * (size_t)kAdjR * kGatherCols * sizeof(float);
+  e = cudaFuncSetAttribute(adj_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tiles = (D + kGatherCols - 1) / kGatherCols;
+  const dim3 grid(nblk, tiles < 65535 ? tiles : 65535);
+  adj_gather_kernel<<<grid, kGatherCols, smem, st>>>(X, N, D, blk_off, blk_nnz, ent, wts, dX);
+  *launches += 7;
   return cudaGetLastError();
 }
 

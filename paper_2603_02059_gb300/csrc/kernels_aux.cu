@@ -126,12 +126,19 @@ __global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
 // neighbour sets, instead of G_ab itself; the epilogue adds groups c_a c_b back in
 // FP32. A permutation of the grid points (the same for every row) leaves the Gram
 // unchanged. With kCorr false (BF16 form) the correction entries and c are zero.
+//
+// With emb > 1 operand row a is the trajectory of emb consecutive days a .. a+emb-1
+// (Eq. 1): its emb * D values are X[a][0..D), X[a+1][0..D), ..., which in the
+// row-major input are the contiguous values X + a*D .. X + (a+emb)*D. The Gram of
+// such rows is the diagonal window sum of Eq. 2 (sum over m of <x_{a+m}, x_{b+m}>),
+// and the norm of a row is the window sum of the day norms.
 template <bool kCorr>
 __global__ void __launch_bounds__(256)
-    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int groups,
-                             const float* __restrict__ mu, const float* __restrict__ wts,
-                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                             double* __restrict__ norms, float* __restrict__ cval) {
+    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int emb,
+                             int groups, const float* __restrict__ mu,
+                             const float* __restrict__ wts, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
+                             float* __restrict__ cval) {
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
@@ -155,8 +162,12 @@ __global__ void __launch_bounds__(256)
   }
   const float* x = si.X + (size_t)a * D;
   const float* m = mu + (size_t)b * D;
+  const int Dlen = emb * D;  // values of one operand row
   // grid-point weights w_p enter the distance as sqrt(w_p) scalings of the values
-  auto val = [&](int i) { return wts ? (x[i] - m[i]) * sqrtf(wts[i]) : x[i] - m[i]; };
+  auto val = [&](int i) {
+    const int pnt = emb > 1 ? i % D : i;  // grid point of value i
+    return wts ? (x[i] - m[pnt]) * sqrtf(wts[pnt]) : x[i] - m[pnt];
+  };
   // One read of the row. Lane g0 + lane builds group g0 + lane: its entry pos is grid
   // point pos * groups + g, so for each pos the warp reads 32 consecutive grid points
   // (coalesced), and each lane writes its group's 64 entries (128 bytes per copy)
@@ -171,8 +182,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int pp = 0; pp < 32; ++pp) {
       const int i0 = (2 * pp) * groups + g, i1 = (2 * pp + 1) * groups + g;
-      const float v0 = i0 < D ? val(i0) : 0.f;
-      const float v1 = (pp < 31 && i1 < D) ? val(i1) : 0.f;  // entry 63 filled later
+      const float v0 = i0 < Dlen ? val(i0) : 0.f;
+      const float v1 = (pp < 31 && i1 < Dlen) ? val(i1) : 0.f;  // entry 63 filled later
       part = fmaf(v0, v0, part);
       part = fmaf(v1, v1, part);
       const __nv_bfloat16 h0 = __float2bfloat16_rn(v0);
@@ -478,17 +489,17 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int groups,
+cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int emb, int groups,
                                      bool correct, const float* mu, const float* wts, void* hi,
                                      void* lo, double* norms, float* cval, cudaStream_t st) {
   const int blocks = (rows + 7) / 8;
   if (correct)
     prep_split_series_kernel<true><<<blocks, 256, 0, st>>>(
-        sr, rows, D, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
+        sr, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
         static_cast<__nv_bfloat16*>(lo), norms, cval);
   else
     prep_split_series_kernel<false><<<blocks, 256, 0, st>>>(
-        sr, rows, D, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
+        sr, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
         static_cast<__nv_bfloat16*>(lo), norms, cval);
   return cudaGetLastError();
 }

@@ -38,6 +38,7 @@ struct TcPlan {
   std::vector<int> slot_lo;
   int rows = 0, out_rows = 0, kmax = 0, Lmax = 0;
   long long part_lists = 0, col_lists = 0;
+  int emb = 1;  // days per operand row (trajectory-embedded operands when > 1)
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
@@ -81,6 +82,7 @@ struct traknn_ctx {
   int seg_k = kSegmentK;
   int group_strips = 0;
   int l2_keep_a = 0;
+  int embed = 0;  // 0: automatic, 1: always, 2: never (TRAKNN_OPT_EMBED)
   const float* weights = nullptr;  // [weights_D] grid-point weights (caller-owned), or null
   int64_t weights_D = 0;
   int stats = 0;
@@ -284,7 +286,7 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
     off += bytes;
     return base + o;
   };
-  b.Dp = tc_groups((int)D) * 64;
+  b.Dp = tc_groups((int)D * p.emb) * 64;
   const int B = p.table.n;
   const size_t ks = (size_t)list_pitch(p.kmax);
   b.partial = reinterpret_cast<float*>(take((size_t)B * kMeanSlices * D * sizeof(float)));
@@ -309,15 +311,16 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
 // Make h->plan the plan for these series (built and uploaded when the shape changes)
 // and size the workspace. Must not run during a stream capture.
 traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
-                         bool shared,
-                         cudaStream_t s, TcBuffers* out) {
+                         bool shared, int emb, cudaStream_t s, TcBuffers* out) {
   std::vector<int64_t> key = shape_key(sd, B, D, h);
   key.push_back(tiles);
   key.push_back(shared ? 1 : 0);
+  key.push_back(emb);
   TcPlan& p = h->plan;
   if (p.key != key) {
     build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, p);
     p.key = key;
+    p.emb = emb;
     const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
     const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
     const size_t sb = align_up(p.slot_lo.size() * sizeof(int), 256);
@@ -388,7 +391,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
 
   const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
   TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
-  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, b.Dp / 64, split, b.mu, h->weights,
+  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, p.emb, b.Dp / 64, split, b.mu,
+                                    h->weights,
                                     b.hi, b.lo,
                                     b.norms, b.cval, s));
   TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s));
@@ -417,6 +421,17 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   return TRAKNN_OK;
 }
 
+
+// Trajectory-embedded operands for a single-series tensor-core call: automatic for
+// small grids, where the fixed per-chunk cost of the epilogue (staging, window sums)
+// and not the contraction decides the time, so L times the Gram work costs little.
+constexpr int64_t kEmbedAutoMaxLD = 1024;    // automatic: L * D at most this
+constexpr int64_t kEmbedMaxLD = 1 << 20;     // forced: L * D at most this
+bool use_embedding(const traknn_ctx* h, int64_t D, int L) {
+  if (L < 2 || h->embed == 2) return false;
+  if (h->embed == 1) return (int64_t)L * D <= kEmbedMaxLD;
+  return (int64_t)L * D <= kEmbedAutoMaxLD;
+}
 
 traknn_status validate_series(const HostSeries* sd, int B, int64_t D) {
   if (B < 1) return TRAKNN_ERR_INVALID_ARG;
@@ -450,7 +465,7 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   int best_t = 8;
   for (int cand : {4, 8, 16}) {
     TcBuffers buf;
-    TRY_ST(prepare_tc(h, sd, B, D, cand, false, s, &buf));
+    TRY_ST(prepare_tc(h, sd, B, D, cand, false, 1, s, &buf));
     TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
     TRY_CUDA(cudaEventRecord(e0, s));
     TRY_ST(enqueue_tc(h, buf, D, s, false));
@@ -473,12 +488,12 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
 // Forward pass of B series on the tensor cores. With `graph` set the launch
 // sequence is captured once per (shape, pointers, options) and replayed.
 traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
-                     bool graph, bool shared = false) {
+                     bool graph, bool shared = false, int emb = 1) {
   if (!tc_available()) return TRAKNN_ERR_UNSUPPORTED;
   int tiles = 8;
-  if (!shared) TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
+  if (!shared && emb == 1) TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
   TcBuffers buf;
-  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, s, &buf));
+  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf));
   if (!graph) return enqueue_tc(h, buf, D, s, h->profile != 0);
 
   std::vector<int64_t> key = h->plan.key;
@@ -640,6 +655,10 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
     case TRAKNN_OPT_L2_KEEP_A:
       h->l2_keep_a = v ? 1 : 0;
       return TRAKNN_OK;
+    case TRAKNN_OPT_EMBED:
+      if (v < 0 || v > 2) return TRAKNN_ERR_INVALID_ARG;
+      h->embed = (int)v;
+      return TRAKNN_OK;
     case TRAKNN_OPT_GROUP_STRIPS:
       if (v < 0 || v > 4096) return TRAKNN_ERR_INVALID_ARG;
       h->group_strips = (int)v;
@@ -681,6 +700,12 @@ traknn_status traknn_knn_scores(traknn_handle h, const float* X, int64_t N, int6
   if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->precision != TRAKNN_PREC_FP32) {
+    if (use_embedding(h, D, L)) {
+      // trajectory-embedded operands: one row per trajectory (L days, contiguous in
+      // X), whose Gram is the window sum itself; the kernels see M rows and L = 1
+      const HostSeries sd{X, N - L + 1, 1, k, e, nbr_idx, nbr_dist, score};
+      return run_tc(h, &sd, 1, D, s, false, false, L);
+    }
     const HostSeries sd{X, N, L, k, e, nbr_idx, nbr_dist, score};
     return run_tc(h, &sd, 1, D, s, false);
   }
@@ -830,7 +855,7 @@ traknn_status traknn_score_backward(traknn_handle h, const float* X, int64_t N, 
   if (N > INT_MAX / 2 || D > INT_MAX / 2) return TRAKNN_ERR_INVALID_ARG;
   if (L > TRAKNN_MAX_L || k > TRAKNN_MAX_K) return TRAKNN_ERR_UNSUPPORTED;
   const int M = (int)(N - L + 1);
-  TRY_ST(ensure_buffer(h, &h->adj, &h->adj_bytes, adjoint_workspace_bytes(M, k)));
+  TRY_ST(ensure_buffer(h, &h->adj, &h->adj_bytes, adjoint_workspace_bytes((int)N, L, k)));
   int launches = 0;
   if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
   TRY_CUDA(launch_adjoint(X, (int)N, (int)D, L, k, nbr_idx, grad_score, h->weights, dX, h->adj,

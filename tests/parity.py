@@ -75,15 +75,16 @@ def check_sampled(X, L, k, e, rows, gidx, gdist, gscore, tol):
 
 
 def structural_rows(M, L, *, n_random=500, seed=0, strip_every=1, col_bounds=(),
-                    extra=()):
+                    extra=(), rows_per_strip=None):
     """Trajectory rows that exercise the kernels' work split at full size.
 
     Output rows are cut into strips of 128 - (L-1) rows (one Gram tile height minus
     the window halo): the first and last row of every `strip_every`-th strip; the
     rows on both sides of each column boundary in `col_bounds` (work-unit and chunk
     edges); the first two and last two rows; `extra` rows; and `n_random` seeded
-    random rows."""
-    R = 128 - (L - 1)
+    random rows. `rows_per_strip` overrides the strip height (128 with
+    trajectory-embedded operands, which have no window halo)."""
+    R = rows_per_strip or 128 - (L - 1)
     rows = [0, 1, M - 2, M - 1]
     for s in range(0, (M + R - 1) // R, strip_every):
         rows += [s * R, min(M - 1, s * R + R - 1)]
@@ -98,7 +99,8 @@ def structural_rows(M, L, *, n_random=500, seed=0, strip_every=1, col_bounds=(),
 
 def tc_unit_bounds(M, L, tiles=8):
     """Column edges of the tensor-core path's work units (tiles Gram tiles of
-    256 - (L-1) output columns each) and of the tiles inside the first unit."""
+    256 - (L-1) output columns each; L = 1 with trajectory-embedded operands) and of
+    the tiles inside the first unit."""
     step = 256 - (L - 1)
     cols = tiles * step
     return sorted(set(list(range(cols, M, cols)) + list(range(step, min(M, cols), step))))

@@ -29,8 +29,10 @@ def _series(shapes, h=9, w=14, seed0=100):
 
 
 def _single(tk, Xd, L, k, e, prec):
+    """The single-series call on the batched path's operands (trajectory-embedded
+    operands off: the batched form never embeds)."""
     import torch
-    idx, dist, score = tk.knn_scores(Xd, L, k, e, precision=prec)
+    idx, dist, score = tk.knn_scores(Xd, L, k, e, precision=prec, embed="never")
     torch.cuda.synchronize()
     return idx.cpu().numpy(), dist.cpu().numpy(), score.cpu().numpy()
 

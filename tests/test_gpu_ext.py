@@ -124,10 +124,10 @@ def test_weights_apply_to_batched_and_multi_calls(tk):
     h = tk.Handle()
     h.set_grid_weights(torch.from_numpy(w).cuda())
     Xs = [torch.from_numpy(make_slp_like(n, 9, 14, seed=70 + n)[0]).cuda() for n in (600, 900)]
-    singles = [tk.knn_scores(X, 4, 8, 3, handle=h) for X in Xs]
+    singles = [tk.knn_scores(X, 4, 8, 3, handle=h, embed="never") for X in Xs]
     batched = tk.knn_scores_batched([(X, 4, 8, 3) for X in Xs], handle=h)
     multi = tk.knn_scores_multi(Xs[1], [(4, 8, 3), (2, 6, 1)], handle=h)
-    single_l2 = tk.knn_scores(Xs[1], 2, 6, 1, handle=h)
+    single_l2 = tk.knn_scores(Xs[1], 2, 6, 1, handle=h, embed="never")
     torch.cuda.synchronize()
     assert h.sync_status() == 0
     for ref, got in zip(singles, batched):

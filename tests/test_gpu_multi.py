@@ -50,7 +50,7 @@ def test_each_setting_agrees_with_its_single_call(tk, symmetric):
     torch.cuda.synchronize()
     assert tk.get_handle().sync_status() == 0
     for (L, k, e), g in zip(SETTINGS, got):
-        ref = tk.knn_scores(Xd, L, k, e, symmetric=symmetric)
+        ref = tk.knn_scores(Xd, L, k, e, symmetric=symmetric, embed="never")
         torch.cuda.synchronize()
         _agree(ref, g, k)
 
@@ -74,7 +74,7 @@ def test_multi_with_segments(tk):
     try:
         h.set_option("segment_k", 512)
         got = tk.knn_scores_multi(Xd, SETTINGS[:4], handle=h)
-        refs = [tk.knn_scores(Xd, L, k, e, handle=h) for L, k, e in SETTINGS[:4]]
+        refs = [tk.knn_scores(Xd, L, k, e, handle=h, embed="never") for L, k, e in SETTINGS[:4]]
         torch.cuda.synchronize()
         assert h.sync_status() == 0
     finally:
@@ -109,7 +109,8 @@ def test_multi_single_product_bf16(tk):
     X, _ = make_slp_like(800, 9, 14, seed=47)
     Xd = torch.from_numpy(X).cuda()
     got = tk.knn_scores_multi(Xd, SETTINGS[:3], precision="bf16")
-    refs = [tk.knn_scores(Xd, L, k, e, precision="bf16") for L, k, e in SETTINGS[:3]]
+    refs = [tk.knn_scores(Xd, L, k, e, precision="bf16", embed="never")
+            for L, k, e in SETTINGS[:3]]
     torch.cuda.synchronize()
     for (L, k, e), ref, g in zip(SETTINGS[:3], refs, got):
         _agree(ref, g, k)

@@ -28,13 +28,15 @@ def _run(tk, X, L, k, e, prec="split_bf16", **kw):
     return idx.cpu().numpy(), dist.cpu().numpy(), score.cpu().numpy()
 
 
+@pytest.mark.parametrize("embed", ["never", "always"])
 @pytest.mark.parametrize("prec", ["split_bf16", "bf16"])
-def test_hand_example_exact(tk, prec):
-    """Small integers are exact in BF16, so both tensor-core forms are exact here."""
+def test_hand_example_exact(tk, prec, embed):
+    """Small integers are exact in BF16, so both tensor-core forms are exact here, with
+    diagonal window sums and with trajectory-embedded operands."""
     Xrows, cases = load_golden("hand_example_6days.txt")
     X = np.array(Xrows, dtype=np.float32)
     for name, (p, rows) in cases.items():
-        idx, dist, score = _run(tk, X, p["L"], p["k"], p["e"], prec, center=False)
+        idx, dist, score = _run(tk, X, p["L"], p["k"], p["e"], prec, center=False, embed=embed)
         for t, (gi, gd, gs) in rows.items():
             assert list(idx[t]) == gi, (name, t)
             assert list(dist[t]) == gd, (name, t)
@@ -58,9 +60,10 @@ def test_small_5y_config_split(tk):
     (1300, 16, 20, 7, 33, 6),
     (900, 8, 10, 4, 45, 3),
 ])
-def test_shapes_split(tk, N, h, w, L, k, e):
+@pytest.mark.parametrize("embed", ["never", "always"])
+def test_shapes_split(tk, N, h, w, L, k, e, embed):
     X, _ = make_slp_like(N, h, w, seed=N + L)
-    idx, dist, score = _run(tk, X, L, k, e)
+    idx, dist, score = _run(tk, X, L, k, e, embed=embed)
     check_full(X, L, k, e, idx, dist, score, TOL["split_bf16"])
 
 
@@ -74,8 +77,8 @@ def test_bf16_error_is_bounded(tk):
 @pytest.mark.parametrize("cols", [256, 300, 700, 5000])
 def test_work_unit_size_is_bitwise_invariant(tk, cols):
     X, _ = make_slp_like(1500, 8, 12, seed=6)
-    ref = _run(tk, X, 5, 10, 4)
-    got = _run(tk, X, 5, 10, 4, unit_cols=cols)
+    ref = _run(tk, X, 5, 10, 4, embed="never")
+    got = _run(tk, X, 5, 10, 4, unit_cols=cols, embed="never")
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
 
@@ -83,15 +86,16 @@ def test_work_unit_size_is_bitwise_invariant(tk, cols):
 @pytest.mark.parametrize("N,h,w,L,k,e", [(1500, 8, 12, 5, 10, 4), (777, 9, 15, 10, 20, 9),
                                          (420, 6, 6, 17, 64, 16), (300, 4, 5, 1, 1, 0),
                                          (1000, 3, 3, 2, 9, 0)])
-def test_symmetric_split_equals_full_evaluation(tk, N, h, w, L, k, e):
+@pytest.mark.parametrize("embed", ["never", "always"])
+def test_symmetric_split_equals_full_evaluation(tk, N, h, w, L, k, e, embed):
     """Evaluating each unordered pair once (upper triangle with column-side lists)
     gives the neighbour lists and scores of evaluating both triangles. D(t,j) and
     D(j,t) come from Gram tiles with the operand roles swapped, so they may differ
     in the last bit: distances agree to 1e-6 and index sets may differ only at
     near ties."""
     X, _ = make_slp_like(N, h, w, seed=N + 2 * L)
-    full = _run(tk, X, L, k, e, symmetric=False)
-    half = _run(tk, X, L, k, e, symmetric=True)
+    full = _run(tk, X, L, k, e, symmetric=False, embed=embed)
+    half = _run(tk, X, L, k, e, symmetric=True, embed=embed)
     rel = np.abs(full[1] - half[1]) / np.maximum(np.abs(full[1]), 1e-30)
     assert rel.max() <= 1e-6
     assert np.allclose(full[2], half[2], rtol=1e-6)
