@@ -165,7 +165,8 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
 
-    X, meta, cfg = config_inputs(args.workload, seed_offset=rank)
+    # weak scaling: every rank its own series; --split: one series shared by all ranks
+    X, meta, cfg = config_inputs(args.workload, seed_offset=0 if args.split else rank)
     N, D = X.shape
     L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
     M = N - L + 1
@@ -178,7 +179,14 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream(device)
 
     def step(prec):
-        tk.knn_scores(Xd, L, k, e, precision=prec, handle=h, out=out)
+        if args.split and prec != "fp32":
+            if ws > 1:
+                tk.knn_scores_split(Xd, L, k, e, precision=prec, handle=h)
+            else:
+                ip, dp = tk.knn_partial(Xd, L, k, e, 0, 1, precision=prec, handle=h)
+                tk.merge_partials(ip[None], dp[None], handle=h)
+        else:
+            tk.knn_scores(Xd, L, k, e, precision=prec, handle=h, out=out)
 
     def timed(prec, steps, warmup, sample_clocks=False):
         for _ in range(warmup):
@@ -213,7 +221,8 @@ def run_ours(args, ws, rank, local):
     # headline: split-BF16 tensor-core path
     head = args.headline
     ms_split, kms_split, launches, clocks = timed(head, args.steps, args.warmup, True)
-    value = aggregate(pairs, ms_split, ws)
+    # split: the ranks share one series' pairs; otherwise every rank resolves its own
+    value = aggregate(pairs / ws if args.split else pairs, ms_split, ws)
     # plain FP32 CUDA-core path on the same input
     fp32_steps = max(1, min(args.steps, args.fp32_steps))
     if args.skip_fp32:
@@ -226,7 +235,7 @@ def run_ours(args, ws, rank, local):
     # algorithmic work = the method's own N(N+1)/2 x 2D (one product per pair)
     peaks, peak_src = measured_peaks()
     products = 3 if head == "split_bf16" else 1
-    algo_flops = N * (N + 1) / 2 * 2 * D
+    algo_flops = N * (N + 1) / 2 * 2 * D / (ws if args.split else 1)  # this rank's share
     flops = algo_flops * products
     kavg = statistics.mean(kms_split) * 1e-3 if kms_split else None
     achieved = flops / kavg / 1e12 if kavg else None
@@ -252,16 +261,18 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the public host-buffer API: pinned X in, results out
     e2e = None
-    if not args.skip_e2e:
+    if not args.skip_e2e and not args.split:  # (the host-buffer call is single-process)
         e2e = run_e2e(tk, h, X, L, k, e, head, args.steps, ws, device)
 
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_split, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if args.split else "weak", "vs_baseline": None,
         "dtype": {"split_bf16": "bf16", "bf16": "bf16", "fp32": "f32"}[head],
-        "data": "synthetic (seeded SLP-like anomalies; one independent series per rank)",
+        "data": ("synthetic (seeded SLP-like anomalies; one series split across the ranks)"
+                 if args.split else
+                 "synthetic (seeded SLP-like anomalies; one independent series per rank)"),
         "config": {"workload": (f"{args.workload}: N={N} days, D={D} ({meta.h}x{meta.w}), "
                                 f"L={L}, k={k}, exclusion={e}, M={M}"),
                    "pairs_per_step": pairs,
@@ -270,7 +281,9 @@ def run_ours(args, ws, rank, local):
                                  "bf16": "BF16 (1 product, FP32 accumulate; FP64 norms)",
                                  "fp32": "FP32 CUDA cores; FP64 norms"}[head],
                    "l2": l2_note(N, D),
-                   "parallelism": f"independent series per rank x{ws}"},
+                   "parallelism": (f"one series, upper-triangle strips split over {ws} ranks, "
+                                   f"candidate lists all-gathered once" if args.split else
+                                   f"independent series per rank x{ws}")},
         "fp32_path": None if ms_fp32 is None else {
             "value": aggregate(pairs, ms_fp32, ws), "ms_per_step": ms_fp32,
             "kernel_ms": statistics.mean(kms_fp32) if kms_fp32 else None, "steps": fp32_steps,
@@ -680,6 +693,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true", help="do not time the FP32 path")
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
+    ap.add_argument("--split", action="store_true",
+                    help="one series shared by all ranks (strong scaling: each rank evaluates "
+                         "its part of the pairs, one all-gather of candidate lists, merge)")
     ap.add_argument("--suite", choices=sorted(SUITES) + ["all"], default=None,
                     help="instead of the headline line, time the extra workloads "
                          "(one JSON line each, one GPU)")

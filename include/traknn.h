@@ -104,6 +104,7 @@ typedef enum {
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */
 #define TRAKNN_MAX_K 64  /* largest neighbour count supported */
+#define TRAKNN_MAX_PARTS 32  /* most parts of one series split across processes */
 
 /* Create a handle on CUDA device `device` (must be compute capability 10.3).
  * Returns TRAKNN_ERR_UNSUPPORTED_DEVICE on any other device. */
@@ -193,6 +194,50 @@ traknn_status traknn_knn_scores_batched(traknn_handle handle, const traknn_serie
  * (TRAKNN_ERR_INVALID_ARG). */
 traknn_status traknn_knn_scores_multi(traknn_handle handle, const traknn_series* settings,
                                       int nset, int64_t D, void* stream);
+
+/* ---- One series split across processes (one GPU each) ------------------------
+ * The unordered trajectory pairs of a series are independent (the upper-triangle
+ * Gram tiles of Sec. 3.3, "Symmetric Batched GeMM"), so P processes can share one
+ * series: each evaluates the pairs of its part (traknn_knn_partial), the per-row
+ * candidate lists are exchanged once (for example an all-gather over the processes),
+ * and every process merges them (traknn_merge_partials) into the exact result of
+ * traknn_knn_scores on the whole series, up to distances evaluated in the other
+ * operand order (a few ulp; neighbour sets may then differ at near ties). */
+
+/* Host-only: the trajectory rows [*row_lo, *row_hi) whose pairs part `part` of
+ * `nparts` evaluates. Rows are cut into strips of 128 - (L-1) rows; each part gets a
+ * contiguous range of strips carrying about 1/nparts of the M(M+1)/2 unordered
+ * pairs (strip s holds the pairs {a, b} with min(a, b) in the strip, b >= a). A part
+ * may be empty (*row_lo == *row_hi) when nparts exceeds the number of strips.
+ * 1 <= L <= TRAKNN_MAX_L, 1 <= nparts <= TRAKNN_MAX_PARTS, 0 <= part < nparts. */
+traknn_status traknn_partition(int64_t M, int L, int nparts, int part, int64_t* row_lo,
+                               int64_t* row_hi);
+
+/* The candidate lists of one part of a split series (tensor-core precisions with the
+ * symmetric evaluation; TRAKNN_ERR_UNSUPPORTED with TRAKNN_PREC_FP32 or
+ * TRAKNN_OPT_SYMMETRIC = 0). Arguments as traknn_knn_scores plus the part:
+ *   part_idx  [M x k] int32 out (device): for every trajectory row t, candidates j of t
+ *             whose pair {t, j} this part evaluates, sorted by (distance, index), at
+ *             least every one of t's k nearest neighbours among them; entries beyond
+ *             the row's candidates hold index -1 and distance +inf
+ *   part_dist [M x k] float32 out (device): their distances D(t, j)
+ * Rows outside the part's strips receive candidates only from pairs whose smaller
+ * index lies in the part (possibly none). */
+traknn_status traknn_knn_partial(traknn_handle handle, const float* X, int64_t N, int64_t D,
+                                 int L, int k, int exclusion, int part, int nparts,
+                                 int32_t* part_idx, float* part_dist, void* stream);
+
+/* Merge the parts' candidate lists (Algorithm 1, kNN step over the union) into the
+ * neighbour sets and rarity scores of Eq. 3:
+ *   idx_parts  [nparts x M x k] int32 (device), part-major: the part_idx of every part
+ *   dist_parts [nparts x M x k] float32 (device): the matching part_dist
+ *   nbr_idx, nbr_dist [M x k], score [M] out (device), as traknn_knn_scores returns them
+ * Each row takes the k smallest (distance, index) entries of the union of its lists;
+ * the score is their FP64 mean. 1 <= nparts <= TRAKNN_MAX_PARTS. */
+traknn_status traknn_merge_partials(traknn_handle handle, const int32_t* idx_parts,
+                                    const float* dist_parts, int nparts, int64_t M, int k,
+                                    int32_t* nbr_idx, float* nbr_dist, float* score,
+                                    void* stream);
 
 /* Grid-point weights: with weights w (D values >= 0, DEVICE pointer, caller-owned,
  * read by every later call on this handle until cleared) the snapshot distance of

@@ -74,6 +74,9 @@ def lib():
                 "traknn_set_grid_weights": [P, P, I64],
                 "traknn_knn_scores_multi": [P, P, I, I64, P],
                 "traknn_knn_stats": [P, P, I64, I, P, I, P, P],
+                "traknn_partition": [I64, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+                "traknn_knn_partial": [P, P, I64, I64, I, I, I, I, I, P, P, P],
+                "traknn_merge_partials": [P, P, P, I, I64, I, P, P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -372,6 +375,81 @@ def knn_scores_static(X: torch.Tensor, L: int, k: int, exclusion: int | None = N
                                             ctypes.c_void_p(s.cuda_stream))
     _check(rc, "traknn_knn_scores_static")
     return idx, dist, score
+
+
+def partition(M: int, L: int, nparts: int, part: int):
+    """Trajectory rows [lo, hi) whose pairs part `part` of `nparts` evaluates when one
+    series is split across processes (host only; see traknn_partition)."""
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().traknn_partition(M, L, nparts, part, ctypes.byref(lo), ctypes.byref(hi)),
+           "traknn_partition")
+    return int(lo.value), int(hi.value)
+
+
+def knn_partial(X: torch.Tensor, L: int, k: int, exclusion: int | None, part: int, nparts: int,
+                *, precision: str = "split_bf16", center: bool = True,
+                handle: Handle | None = None):
+    """Candidate lists ([M, k] int32 indices, -1 = none; [M, k] float32 distances) of
+    part `part` of `nparts` of one series split across processes."""
+    X = _as_input(X)
+    N, D = X.shape
+    e = L - 1 if exclusion is None else int(exclusion)
+    M = N - L + 1
+    h = handle or get_handle(X.device.index)
+    h.configure(precision=precision, center=center, symmetric=True, unit_cols=0)
+    idx = torch.empty((M, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((M, k), dtype=torch.float32, device=X.device)
+    s = torch.cuda.current_stream(X.device)
+    rc = lib().traknn_knn_partial(h._h, X.data_ptr(), N, D, L, k, e, part, nparts,
+                                  idx.data_ptr(), dist.data_ptr(), ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_knn_partial")
+    return idx, dist
+
+
+def merge_partials(idx_parts: torch.Tensor, dist_parts: torch.Tensor, *,
+                   handle: Handle | None = None):
+    """Neighbour indices, distances and scores from the parts' candidate lists
+    ([P, M, k] int32 and float32 CUDA tensors, part-major)."""
+    if idx_parts.dim() != 3 or dist_parts.shape != idx_parts.shape or not idx_parts.is_cuda:
+        raise ValueError("idx_parts and dist_parts must be [P, M, k] CUDA tensors")
+    idx_parts = idx_parts.to(torch.int32).contiguous()
+    dist_parts = dist_parts.to(torch.float32).contiguous()
+    P, M, k = idx_parts.shape
+    h = handle or get_handle(idx_parts.device.index)
+    idx = torch.empty((M, k), dtype=torch.int32, device=idx_parts.device)
+    dist = torch.empty((M, k), dtype=torch.float32, device=idx_parts.device)
+    score = torch.empty((M,), dtype=torch.float32, device=idx_parts.device)
+    s = torch.cuda.current_stream(idx_parts.device)
+    rc = lib().traknn_merge_partials(h._h, idx_parts.data_ptr(), dist_parts.data_ptr(), P, M, k,
+                                     idx.data_ptr(), dist.data_ptr(), score.data_ptr(),
+                                     ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "traknn_merge_partials")
+    return idx, dist, score
+
+
+def gather_partials(idx: torch.Tensor, dist: torch.Tensor, group=None):
+    """The exchange step of a split series: every process's [M, k] candidate lists,
+    gathered from all processes of `group` (torch.distributed) into [P, M, k] tensors
+    in rank order (the part index is the rank)."""
+    import torch.distributed as dist_
+    P = dist_.get_world_size(group)
+    ilist = [torch.empty_like(idx) for _ in range(P)]
+    dlist = [torch.empty_like(dist) for _ in range(P)]
+    dist_.all_gather(ilist, idx.contiguous(), group=group)
+    dist_.all_gather(dlist, dist.contiguous(), group=group)
+    return torch.stack(ilist), torch.stack(dlist)
+
+
+def knn_scores_split(X: torch.Tensor, L: int, k: int, exclusion: int | None = None, *,
+                     group=None, precision: str = "split_bf16", handle: Handle | None = None):
+    """traknn_knn_scores on one series shared by the processes of `group`: this
+    process evaluates the pairs of its part (part = rank), the candidate lists are
+    all-gathered once, and every process merges them into the full result."""
+    import torch.distributed as dist_
+    rank, P = dist_.get_rank(group), dist_.get_world_size(group)
+    pidx, pdist = knn_partial(X, L, k, exclusion, rank, P, precision=precision, handle=handle)
+    iparts, dparts = gather_partials(pidx, pdist, group)
+    return merge_partials(iparts, dparts, handle=handle)
 
 
 def score_backward(X: torch.Tensor, L: int, k: int, idx: torch.Tensor,

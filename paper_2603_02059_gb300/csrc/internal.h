@@ -131,7 +131,7 @@ struct SeriesInfo {
   int N, M, L, k;
   int e;
   int rows_out;         // output rows per strip: 128 - (L-1), or less when series share tiles
-  int step;             // output columns per Gram tile: 256 - (L-1), or less likewise
+  int step;             // output columns of a one-tile unit: 256 - (L-1), or less likewise
   int row_base;         // first stacked operand row (day 0 of the series)
   int out_base;         // first stacked trajectory row
   int slots;            // row-side list slots per trajectory row
@@ -181,6 +181,10 @@ struct TcWork {
   int* counter;             // next unit to hand out (zero before the launch)
   int write_lists;          // 0: only publish row bounds (band pre-pass)
   unsigned long long* stats;  // optional event counters (see kStat*), nullptr = off
+  // Strips [part_lo, part_hi) of the (single) series were evaluated by this call (one
+  // part of a series split across processes); the merge reads only their lists.
+  // Every other call: 0 and INT_MAX.
+  int part_lo, part_hi;
 };
 
 struct TcArgs {
@@ -250,6 +254,26 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
 // Operand layout of the tensor-core path: groups = ceil(D / 63) groups of 64 K
 // entries (63 permuted grid points + 1 correction entry); pitch groups * 64.
 inline int tc_groups(int D) { return (D + 62) / 63; }
+
+// Split of one series' upper-triangle work over `nparts` processes: contiguous ranges
+// of row strips (strip height R = 128 - (L-1)) with about equal work, strip s holding
+// (M - s R) R of the M (M+1)/2 unordered pairs. Strips [*s_lo, *s_hi) go to `part`;
+// an unordered pair {a, b} is evaluated in the part whose strips hold min(a, b).
+inline void split_strips(long long M, int L, int nparts, int part, int* s_lo, int* s_hi) {
+  const long long R = kTileRows - (L - 1);
+  const long long S = (M + R - 1) / R;
+  long long total = 0;
+  for (long long s = 0; s < S; ++s) total += M - s * R;
+  auto first = [&](int p) -> int {  // first strip of part p: cumulative work >= p/nparts
+    if (p <= 0) return 0;
+    if (p >= nparts) return (int)S;
+    long long cum = 0, s = 0;
+    while (s < S && cum * nparts < (long long)p * total) cum += M - (s++) * R;
+    return (int)s;
+  };
+  *s_lo = first(part);
+  *s_hi = first(part + 1);
+}
 // emb > 1: each operand row is the emb-day trajectory starting at that day (emb * D
 // values, contiguous in X); the series table then describes trajectories (N = M, L = 1).
 cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int emb, int groups,
@@ -259,6 +283,11 @@ cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const doub
                                  float* W, cudaStream_t st);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
                          cudaStream_t st);
+// Exact top-k of the union of nparts sorted candidate lists per row ([nparts][M][k],
+// index -1 = empty entry), with the rarity score (FP64 mean); nparts <= 32.
+cudaError_t launch_merge_parts(const int32_t* idx_parts, const float* dist_parts, int nparts,
+                               int M, int k, int32_t* idx, float* dist, float* score,
+                               cudaStream_t st);
 // Adjoint of the summed weighted score (kernels_adjoint.cu); `ws` must hold
 // adjoint_workspace_bytes(N, L, k) bytes. Adds the number of launches to *launches.
 size_t adjoint_workspace_bytes(int N, int L, int k);

@@ -183,9 +183,11 @@ __device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr,
   us.slot = wu.slot;
   us.step = si.step;
   if (us.jlo >= us.jhi) return false;
-  // tiles overlap by at least L-1 Gram columns so that each one holds the whole
-  // window of its `step` output columns
-  us.ntiles = (us.jhi - us.jlo + us.step - 1) / us.step;
+  // Gram tiles follow each other without overlap: tile it covers Gram columns
+  // [jlo + 256 it, jlo + 256 (it+1)); the epilogue carries the last L-1 columns of
+  // a tile into the next, so the windows of all output columns [jlo, jhi) are
+  // complete once Gram column jhi + L - 2 is in
+  us.ntiles = (us.jhi - us.jlo + us.L - 1 + BN - 1) / BN;
   return true;
 }
 
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (u >= w.nunits) break;
         if (!unit_span(w, p.sr.s, u, 0, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
-          const int c0 = us.row_base + us.jlo + it * us.step;
+          const int c0 = us.row_base + us.jlo + it * BN;
           const int a0 = us.row_base + us.T0;
           for (int kb = 0; kb < nkb; ++kb) {
             if (!wait_bounded(empty0 + 8u * stage, phase ^ 1u, ctl)) {
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int jsym = us.T0 + us.R;  // column side from here on (sym)
         const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
         if (nser > 1 || it == 0) list.reset();
-        const int c0 = us.jlo + it * us.step;
+        const int c0 = us.jlo + it * BN;
         // W and row bounds of this tile's output columns j = c0 - (L-1) + x (the
         // previous tile's readers passed its last barrier)
         for (int x = et; x < BN; x += kEpiThreads) {
@@ -626,7 +628,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               load_scr(gt, ch, vr);
           }
           float* grow = Gbuf + l * LDG;
-          if (ch > 0)
+          // the diagonal carry: the last L-1 Gram columns of the previous chunk (of
+          // the previous tile of this unit at ch = 0) start this chunk's windows
+          if (ch > 0 || it > 0)
             for (int c = 0; c < L - 1; ++c) grow[c] = grow[32 + c];
           const float* cs = Csh + ch * 32;
           // Gram values of the chunk (correction added back): staged in shared memory
@@ -666,15 +670,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           lap(3);
           const int j0 = c0 + ch * 32 - (L - 1);
           // column side of this chunk: output columns j >= jsym inside the unit
+          // the first L-1 columns of a unit's first chunk have no carried window
+          const int xfirst = (ch == 0 && it == 0) ? L - 1 : 0;
           const uint32_t colrange = w.sym ? bit_range(max(jsym, us.jlo) - j0, us.jhi - j0) &
-                                                bit_range(ch == 0 ? L - 1 : 0, 32)
+                                                bit_range(xfirst, 32)
                                           : 0u;
           uint32_t cand = 0, ccand = 0;
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
             // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
-            uint32_t valid = bit_range(ch == 0 ? L - 1 : 0, 32) &
-                             bit_range(us.jlo - j0, us.jhi - j0);
+            uint32_t valid = bit_range(xfirst, 32) & bit_range(us.jlo - j0, us.jhi - j0);
             valid &= ~bit_range(t - us.e - j0, t + us.e + 1 - j0);  // exclusion zone
             const float* g0 = Gbuf + l * LDG;
             const float* wv = Wsh + ch * 32;

@@ -181,16 +181,24 @@ __global__ void __launch_bounds__(kBuildThreads)
                      AdjEntry* __restrict__ ent) {
   __shared__ unsigned long long key[kKeyCap];
   __shared__ int dayoff[kAdjR + 1];  // first position of each day in the block
+  __shared__ int soff[kAdjR + kMaxL + 1];  // off[j] for the window days j of the block
   __shared__ int scan[kBuildThreads];
   const int tid = threadIdx.x;
   const int a0 = blockIdx.x * kAdjR;
   const int nd = min(kAdjR, N - a0);
   const float inv_k2 = 2.0f / (float)k;
+  // window days of the block's days: [jb, je]; their reverse-list offsets off[jb..je+1]
+  const int jb = max(0, a0 - L + 1), je = min(a0 + nd - 1, M - 1);
+  for (int i = tid; i <= je - jb + 1; i += kBuildThreads) soff[i] = off[jb + i];
+  __syncthreads();
+  auto offj = [&](int j) { return soff[j - jb]; };  // off[j], jb <= j <= je + 1
   if (tid == 0) {
     int pos = 0;
     for (int d = 0; d < nd; ++d) {
       dayoff[d] = pos;
-      pos += day_incidences(off, a0 + d, L, M, k);
+      const int a = a0 + d;
+      const int t_lo = max(0, a - L + 1), t_hi = min(a, M - 1);
+      if (t_hi >= t_lo) pos += (t_hi - t_lo + 1) * k + (offj(t_hi + 1) - offj(t_lo));
     }
     dayoff[nd] = pos;
   }
@@ -209,9 +217,9 @@ __global__ void __launch_bounds__(kBuildThreads)
       b = j + a - t;
       return j >= 0 && j < M;
     }
-    const int r = off[t_lo] + (q - nfwd);  // reverse lists of t_lo..t_hi are contiguous
+    const int r = offj(t_lo) + (q - nfwd);  // reverse lists of t_lo..t_hi are contiguous
     int j = t_lo;
-    while (off[j + 1] <= r) ++j;
+    while (offj(j + 1) <= r) ++j;
     t = rev[r];
     kind = 1;
     slot = j - t_lo;
@@ -325,6 +333,7 @@ __global__ void __launch_bounds__(kGatherCols)
   extern __shared__ float adj_sm[];
   float(*xa)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm);
   float(*acc)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm + kAdjR * kGatherCols);
+  int4* ebuf = reinterpret_cast<int4*>(adj_sm + 2 * kAdjR * kGatherCols);  // [kGatherCols]
   const int tid = threadIdx.x;
   const int a0 = blockIdx.x * kAdjR;
   const int nd = min(kAdjR, N - a0);
@@ -340,25 +349,31 @@ __global__ void __launch_bounds__(kGatherCols)
       acc[d][tid] = 0.f;
     }
     const float* xp = X + (pin ? p : 0);
-    constexpr int U = 8;  // entries whose partner values are loaded together
-    int q = 0;
-    for (; q + U <= n; q += U) {
-      int4 e[U];
-      float xb[U];
+    // entries are staged kGatherCols at a time (one coalesced load per thread) and
+    // then read from shared memory by every thread; partner values are loaded U at
+    // a time so that U loads per thread are in flight
+    for (int q0 = 0; q0 < n; q0 += kGatherCols) {
+      const int nq = min(kGatherCols, n - q0);
+      __syncthreads();  // the previous chunk's entries have been read
+      if (tid < nq) ebuf[tid] = __ldg(e4 + q0 + tid);
+      __syncthreads();
+      constexpr int U = 16;
+      int q = 0;
+      for (; q + U <= nq; q += U) {
+        float xb[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) e[u] = __ldg(e4 + q + u);
+        for (int u = 0; u < U; ++u) xb[u] = pin ? __ldg(xp + (size_t)ebuf[q + u].x * D) : 0.f;
 #pragma unroll
-      for (int u = 0; u < U; ++u) xb[u] = pin ? __ldg(xp + (size_t)e[u].x * D) : 0.f;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int d = e[u].y;
-        acc[d][tid] = fmaf(__int_as_float(e[u].z), xa[d][tid] - xb[u], acc[d][tid]);
+        for (int u = 0; u < U; ++u) {
+          const int4 e = ebuf[q + u];
+          acc[e.y][tid] = fmaf(__int_as_float(e.z), xa[e.y][tid] - xb[u], acc[e.y][tid]);
+        }
       }
-    }
-    for (; q < n; ++q) {
-      const int4 e = __ldg(e4 + q);
-      const float xb = pin ? __ldg(xp + (size_t)e.x * D) : 0.f;
-      acc[e.y][tid] = fmaf(__int_as_float(e.z), xa[e.y][tid] - xb, acc[e.y][tid]);
+      for (; q < nq; ++q) {
+        const int4 e = ebuf[q];
+        const float xb = pin ? __ldg(xp + (size_t)e.x * D) : 0.f;
+        acc[e.y][tid] = fmaf(__int_as_float(e.z), xa[e.y][tid] - xb, acc[e.y][tid]);
+      }
     }
     if (pin) {
       const float wp = wts ? wts[p] : 1.f;
@@ -422,7 +437,7 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_block_scan_kernel<<<1, 1024, 0, st>>>(off, N, L, M, k, nblk, blk_off);
   adj_build_kernel<<<nblk, kBuildThreads, 0, st>>>(idx, g, N, L, M, k, off, rev, blk_off,
                                                     blk_nnz, ent);
-  const size_t smem = 2 * (size_t)kAdjR * kGatherCols * sizeof(float);
+  const size_t smem = 2 * (size_t)kAdjR * kGatherCols * sizeof(float) + kGatherCols * 16;
   e = cudaFuncSetAttribute(adj_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;

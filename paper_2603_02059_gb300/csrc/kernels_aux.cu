@@ -292,6 +292,54 @@ __global__ void merge_kernel(const float* __restrict__ part_d, const int32_t* __
   if (lane == 0) score[t] = (float)(sum / (double)k);
 }
 
+// One warp per trajectory row: the exact top-k of the union of the row's candidate
+// lists from the parts of a split series ([nparts][M][k], each sorted by (distance,
+// index), index -1 = empty). Every unordered pair was evaluated by exactly one part,
+// so the lists are disjoint; lane p walks list p and k rounds of a warp arg-min on
+// (distance, index) take the smallest. The score is the FP64 mean (Eq. 3).
+__global__ void merge_parts_kernel(const int32_t* __restrict__ pidx,
+                                   const float* __restrict__ pdist, int P, int M, int k,
+                                   int32_t* __restrict__ idx, float* __restrict__ dist,
+                                   float* __restrict__ score) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= M) return;
+  const size_t base = ((size_t)lane * M + t) * k;
+  int cur = 0;
+  double sum = 0.0;
+  for (int r = 0; r < k; ++r) {
+    float hd = CUDART_INF_F;
+    int hidx = INT_MAX;
+    if (lane < P && cur < k) {
+      const int ii = pidx[base + cur];
+      if (ii >= 0) {
+        hd = pdist[base + cur];
+        hidx = ii;
+      }
+    }
+    float bd = hd;
+    int bi = hidx, bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (od < bd || (od == bd && (oi < bi || (oi == bi && ol < bl)))) {
+        bd = od;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    if (lane == bl) ++cur;
+    if (lane == 0) {
+      idx[(size_t)t * k + r] = bi == INT_MAX ? -1 : bi;
+      dist[(size_t)t * k + r] = bd;
+      sum += (double)bd;
+    }
+  }
+  if (lane == 0) score[t] = (float)(sum / (double)k);
+}
+
 constexpr int kMergeWarps = 8;
 constexpr int kMergeCap = 256;
 
@@ -362,12 +410,16 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     }
     return last_d;
   };
+  // with a split series only the lists of this call's strips exist
+  const bool own = strip >= w.part_lo && strip < w.part_hi;
+  const int s2_lo = w.part_lo, s2_hi = min(strip, w.part_hi);
+  const int c_hi = own ? si.slots : c_lo;
   int n = 0;
   for (int pass = 0; pass < 64; ++pass) {
     if (lane == 0) bn[wid] = 0;
     __syncwarp();
     // lists are read four entries at a time (the list pitch ks is a multiple of 4)
-    for (int c = c_lo + lane; c < si.slots; c += 32) {
+    for (int c = c_lo + lane; c < c_hi; c += 32) {
       const size_t b = (size_t)(plist + c) * ks;
       const float4* d4 = reinterpret_cast<const float4*>(part_d + b);
       const int4* i4 = reinterpret_cast<const int4*>(part_i + b);
@@ -389,7 +441,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
     }
     if (w.sym) {
-      for (int s2 = lane; s2 < strip; s2 += 32) {
+      for (int s2 = s2_lo + lane; s2 < s2_hi; s2 += 32) {
         const long long li = collist(s2);
         const int nn = w.col_n[li];
         const float4* d4 = reinterpret_cast<const float4*>(w.col_d + li * ks);
@@ -431,7 +483,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     if (!direct) {
       for (int q = lane; q < n; q += 32) consider(bd[wid][q], bi[wid][q]);
     } else {
-      for (int c = c_lo + lane; c < si.slots; c += 32) {
+      for (int c = c_lo + lane; c < c_hi; c += 32) {
         const size_t b = (size_t)(plist + c) * ks;
         for (int p = 0; p < k; ++p) {
           const int ii = part_i[b + p];
@@ -440,7 +492,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
         }
       }
       if (w.sym) {
-        for (int s2 = lane; s2 < strip; s2 += 32) {
+        for (int s2 = s2_lo + lane; s2 < s2_hi; s2 += 32) {
           const long long li = collist(s2);
           const int nn = w.col_n[li];
           for (int p = 0; p < nn; ++p) {
@@ -475,6 +527,16 @@ cudaError_t launch_merge_tc(const TcArgs& a, const TcWork& w, const SeriesTable&
                             cudaStream_t st) {
   const int blocks = (a.out_rows + kMergeWarps - 1) / kMergeWarps;
   merge_tc_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(a.part_d, a.part_i, a.out_rows, w, sr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_parts(const int32_t* idx_parts, const float* dist_parts, int nparts,
+                               int M, int k, int32_t* idx, float* dist, float* score,
+                               cudaStream_t st) {
+  if (nparts < 1 || nparts > 32) return cudaErrorInvalidValue;
+  const int blocks = (M + kMergeWarps - 1) / kMergeWarps;
+  merge_parts_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(idx_parts, dist_parts, nparts, M, k,
+                                                          idx, dist, score);
   return cudaGetLastError();
 }
 

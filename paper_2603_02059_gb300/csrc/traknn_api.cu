@@ -39,6 +39,7 @@ struct TcPlan {
   int rows = 0, out_rows = 0, kmax = 0, Lmax = 0;
   long long part_lists = 0, col_lists = 0;
   int emb = 1;  // days per operand row (trajectory-embedded operands when > 1)
+  int part_lo = 0, part_hi = INT_MAX;  // strips evaluated (one part of a split series)
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
@@ -144,8 +145,9 @@ static_assert(sizeof(WorkUnit) == 32, "work unit layout");
 inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
 
 // Tensor-core work list of a batch. For each series: strips of 128 - (L-1) output
-// rows; units of `tiles` Gram tiles (each yielding kTileCols - (L-1) output columns);
-// with the symmetric split only columns from each strip's own block on. Units
+// rows; units of `tiles` Gram tiles (tiles * kTileCols - (L-1) output columns: the
+// epilogue carries the last L-1 Gram columns of a tile into the next); with the
+// symmetric split only columns from each strip's own block on. Units
 // are ordered per series in groups of strips that run side by side (sharing A and
 // B tiles in L2), the groups from the last strip upwards. The band units (two
 // tiles of columns centred on each strip's rows) seed the row bounds first.
@@ -156,7 +158,7 @@ inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
 // unit is one tile long and carries all B series (pad[0] = B), and the first series
 // (smallest L, most trajectories) defines the units' column ranges.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
-                int group_opt, bool shared, TcPlan& p) {
+                int group_opt, bool shared, int part_lo, int part_hi, TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
@@ -175,7 +177,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     const int R = kTileRows - (Lg - 1);
     const int step = kTileCols - (Lg - 1);
     const int strips = (M + R - 1) / R;
-    const int cols = shared ? step : cols_opt > 0 ? cols_opt : tiles * step;
+    const int cols = shared ? step : cols_opt > 0 ? cols_opt : tiles * kTileCols - (Lg - 1);
     const int slots = (M + cols - 1) / cols;
     SeriesInfo& si = p.table.s[b];
     si.N = N;
@@ -206,16 +208,16 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
         const int g = sym ? ngroups - 1 - gi : gi;
         const int s_lo = g * group, s_hi = std::min(strips, s_lo + group);
         for (int c = 0; c < slots; ++c)
-          for (int s = s_lo; s < s_hi; ++s) {
+          for (int s = std::max(s_lo, part_lo); s < std::min(s_hi, part_hi); ++s) {
             int jlo = c * cols;
             const int jhi = std::min(M, (c + 1) * cols);
             if (sym) jlo = std::max(jlo, s * R);
             if (jlo < jhi) p.units.push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
           }
       }
-      // band: two tiles of columns centred on the strip's rows
+      // band: two tiles of columns (2 kTileCols - (L-1) outputs) centred on the strip's rows
       const int bw = std::max(0, (2 * kTileCols - (Lg - 1) - R) / 2);
-      for (int s = 0; s < strips; ++s) {
+      for (int s = std::max(0, part_lo); s < std::min(strips, part_hi); ++s) {
         const int T0 = s * R;
         const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
         if (jlo < jhi) band.push_back(WorkUnit{b, s, jlo, jhi, 0, {nser, 0, 0}});
@@ -273,6 +275,7 @@ struct TcBuffers {
   int32_t* col_i;
   int* counter;
   float* scratch;
+  float* pscore;  // [out_rows] scores of partial lists (split series), not returned
   int Dp;
   size_t total;
 };
@@ -304,6 +307,7 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
   b.col_i = reinterpret_cast<int32_t*>(take((size_t)p.col_lists * ks * sizeof(int32_t)));
   b.counter = reinterpret_cast<int*>(take(256));
   b.scratch = reinterpret_cast<float*>(take(tc_scratch_bytes(num_ctas)));
+  b.pscore = reinterpret_cast<float*>(take((size_t)p.out_rows * sizeof(float)));
   b.total = off;
   return b;
 }
@@ -311,16 +315,22 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
 // Make h->plan the plan for these series (built and uploaded when the shape changes)
 // and size the workspace. Must not run during a stream capture.
 traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
-                         bool shared, int emb, cudaStream_t s, TcBuffers* out) {
+                         bool shared, int emb, cudaStream_t s, TcBuffers* out,
+                         int part_lo = 0, int part_hi = INT_MAX) {
   std::vector<int64_t> key = shape_key(sd, B, D, h);
   key.push_back(tiles);
   key.push_back(shared ? 1 : 0);
   key.push_back(emb);
+  key.push_back(part_lo);
+  key.push_back(part_hi);
   TcPlan& p = h->plan;
   if (p.key != key) {
-    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, p);
+    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, part_lo, part_hi,
+               p);
     p.key = key;
     p.emb = emb;
+    p.part_lo = part_lo;
+    p.part_hi = part_hi;
     const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
     const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
     const size_t sb = align_up(p.slot_lo.size() * sizeof(int), 256);
@@ -344,6 +354,8 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   const TcBuffers probe = tc_layout(p, D, h->sm_count, nullptr);
   TRY_ST(ensure_buffer(h, &h->tcws, &h->tcws_bytes, probe.total));
   *out = tc_layout(p, D, h->sm_count, static_cast<char*>(h->tcws));
+  for (int b = 0; b < B; ++b)  // partial lists: their scores go to the workspace
+    if (!p.table.s[b].score) p.table.s[b].score = out->pscore + p.table.s[b].out_base;
   return TRAKNN_OK;
 }
 
@@ -388,6 +400,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   w.counter = b.counter;
   w.write_lists = 1;
   w.stats = h->stats ? h->stats_dev : nullptr;
+  w.part_lo = p.part_lo;
+  w.part_hi = p.part_hi;
 
   const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
   TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
@@ -488,12 +502,14 @@ traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
 // Forward pass of B series on the tensor cores. With `graph` set the launch
 // sequence is captured once per (shape, pointers, options) and replayed.
 traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
-                     bool graph, bool shared = false, int emb = 1) {
+                     bool graph, bool shared = false, int emb = 1, int part_lo = 0,
+                     int part_hi = INT_MAX) {
   if (!tc_available()) return TRAKNN_ERR_UNSUPPORTED;
   int tiles = 8;
-  if (!shared && emb == 1) TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
+  const bool whole = part_lo == 0 && part_hi == INT_MAX;
+  if (!shared && emb == 1 && whole) TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
   TcBuffers buf;
-  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf));
+  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi));
   if (!graph) return enqueue_tc(h, buf, D, s, h->profile != 0);
 
   std::vector<int64_t> key = h->plan.key;
@@ -793,6 +809,50 @@ traknn_status traknn_knn_scores_multi(traknn_handle h, const traknn_series* sett
   std::stable_sort(sd.begin(), sd.end(),
                    [](const HostSeries& x, const HostSeries& y) { return x.L < y.L; });
   return run_tc(h, sd.data(), nset, D, s, false, true);
+}
+
+traknn_status traknn_partition(int64_t M, int L, int nparts, int part, int64_t* row_lo,
+                               int64_t* row_hi) {
+  if (!row_lo || !row_hi || M < 1 || M > INT_MAX / 2 || L < 1 || L > TRAKNN_MAX_L ||
+      nparts < 1 || nparts > TRAKNN_MAX_PARTS || part < 0 || part >= nparts)
+    return TRAKNN_ERR_INVALID_ARG;
+  int s_lo = 0, s_hi = 0;
+  split_strips(M, L, nparts, part, &s_lo, &s_hi);
+  const int64_t R = kTileRows - (L - 1);
+  *row_lo = std::min<int64_t>(M, s_lo * R);
+  *row_hi = std::min<int64_t>(M, s_hi * R);
+  return TRAKNN_OK;
+}
+
+traknn_status traknn_knn_partial(traknn_handle h, const float* X, int64_t N, int64_t D, int L,
+                                 int k, int e, int part, int nparts, int32_t* part_idx,
+                                 float* part_dist, void* stream) {
+  TRY_ST(check_handle(h));
+  if (!X || !part_idx || !part_dist) return TRAKNN_ERR_INVALID_ARG;
+  TRY_ST(traknn_check_problem(N, D, L, k, e));
+  if (nparts < 1 || nparts > TRAKNN_MAX_PARTS || part < 0 || part >= nparts)
+    return TRAKNN_ERR_INVALID_ARG;
+  if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
+  if (h->precision == TRAKNN_PREC_FP32 || !h->sym) return TRAKNN_ERR_UNSUPPORTED;
+  int s_lo = 0, s_hi = 0;
+  split_strips(N - L + 1, L, nparts, part, &s_lo, &s_hi);
+  const HostSeries sd{X, N, L, k, e, part_idx, part_dist, nullptr};
+  return run_tc(h, &sd, 1, D, static_cast<cudaStream_t>(stream), false, false, 1, s_lo, s_hi);
+}
+
+traknn_status traknn_merge_partials(traknn_handle h, const int32_t* idx_parts,
+                                    const float* dist_parts, int nparts, int64_t M, int k,
+                                    int32_t* nbr_idx, float* nbr_dist, float* score,
+                                    void* stream) {
+  TRY_ST(check_handle(h));
+  if (!idx_parts || !dist_parts || !nbr_idx || !nbr_dist || !score) return TRAKNN_ERR_INVALID_ARG;
+  if (nparts < 1 || nparts > TRAKNN_MAX_PARTS || M < 1 || M > INT_MAX / 2 || k < 1 ||
+      k > TRAKNN_MAX_K)
+    return TRAKNN_ERR_INVALID_ARG;
+  TRY_CUDA(launch_merge_parts(idx_parts, dist_parts, nparts, (int)M, k, nbr_idx, nbr_dist, score,
+                              static_cast<cudaStream_t>(stream)));
+  h->launches += 1;
+  return TRAKNN_OK;
 }
 
 traknn_status traknn_set_grid_weights(traknn_handle h, const float* weights, int64_t D) {

@@ -98,12 +98,13 @@ def structural_rows(M, L, *, n_random=500, seed=0, strip_every=1, col_bounds=(),
 
 
 def tc_unit_bounds(M, L, tiles=8):
-    """Column edges of the tensor-core path's work units (tiles Gram tiles of
-    256 - (L-1) output columns each; L = 1 with trajectory-embedded operands) and of
-    the tiles inside the first unit."""
-    step = 256 - (L - 1)
-    cols = tiles * step
-    return sorted(set(list(range(cols, M, cols)) + list(range(step, min(M, cols), step))))
+    """Column edges of the tensor-core path's work units (tiles consecutive Gram tiles
+    of 256 columns, tiles * 256 - (L-1) output columns; L = 1 with trajectory-embedded
+    operands) and of the tiles inside the first unit (the first yields 256 - (L-1)
+    output columns, the later ones 256 each, the last L-1 Gram columns carried)."""
+    cols = tiles * 256 - (L - 1)
+    inner = range(256 - (L - 1), min(M, cols), 256)
+    return sorted(set(list(range(cols, M, cols)) + list(inner)))
 
 
 def fp32_chunk_bounds(M, chunks=8):
