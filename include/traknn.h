@@ -52,8 +52,10 @@ typedef enum {
   TRAKNN_ERR_TIMEOUT = 5,            /* a bounded device-side wait ran out */
   TRAKNN_ERR_UNSUPPORTED_DEVICE = 6, /* the device is not sm_103 */
   TRAKNN_ERR_UNSUPPORTED = 7,        /* L or k above the compiled limits below */
-  TRAKNN_ERR_SCRATCH_LIMIT = 8       /* traknn_knn_scores_static: the problem needs more scratch
+  TRAKNN_ERR_SCRATCH_LIMIT = 8,      /* traknn_knn_scores_static: the problem needs more scratch
                                         than the library's fixed device array holds */
+  TRAKNN_ERR_BOUNDS = 9              /* debug build (libtraknn_bounds.so) only: a device-side
+                                        index check failed; the access was skipped */
 } traknn_status;
 
 /* Arithmetic of the snapshot Gram contraction (the dominant step, Sec. 3.3,
@@ -68,7 +70,8 @@ typedef enum {
 typedef enum {
   TRAKNN_OPT_PRECISION = 0,          /* a traknn_precision value (default SPLIT_BF16) */
   TRAKNN_OPT_CENTER = 1,             /* 1: subtract the per-grid-point mean over days before the
-                                        Gram (exact by the offset invariance of Eq. 2; default 1) */
+                                        Gram (days 0, s, 2s, ..., at most 4,096 of them; exact by
+                                        the offset invariance of Eq. 2 whatever the mean; default 1) */
   TRAKNN_OPT_COL_CHUNKS = 2,         /* column chunks per row strip, 0 = automatic */
   TRAKNN_OPT_WAIT_LIMIT_MS = 3,      /* limit of every device spin-wait in ms (default 2000) */
   TRAKNN_OPT_DEBUG_WITHHOLD = 4,     /* test hook: 1 makes the tensor-core kernel's producer withhold

@@ -21,7 +21,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "traknn.h")
 
 STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_TOO_FEW_CANDIDATES", 3: "ERR_ALLOC",
           4: "ERR_CUDA", 5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED_DEVICE", 7: "ERR_UNSUPPORTED",
-          8: "ERR_SCRATCH_LIMIT"}
+          8: "ERR_SCRATCH_LIMIT", 9: "ERR_BOUNDS"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "bf16": 2}
 EMBED = {"auto": 0, "always": 1, "never": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
@@ -55,37 +55,43 @@ def lib():
             if not os.path.exists(LIB_PATH):
                 raise RuntimeError(f"{LIB_PATH} is missing: build it with "
                                    "`python -c 'import __graft_entry__ as g; g.build()'`")
-            L = ctypes.CDLL(LIB_PATH)
-            P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
-            sig = {
-                "traknn_create": [ctypes.POINTER(P), I],
-                "traknn_destroy": [P],
-                "traknn_set_option": [P, I, I64],
-                "traknn_check_problem": [I64, I64, I, I, I],
-                "traknn_knn_scores": [P, P, I64, I64, I, I, I, P, P, P, P],
-                "traknn_knn_scores_host": [P, P, I64, I64, I, I, I, P, P, P, P],
-                "traknn_score_backward": [P, P, I64, I64, I, I, P, P, P, P],
-                "traknn_sync_status": [P, P],
-                "traknn_profile_read": [P, P, I, ctypes.POINTER(I)],
-                "traknn_launch_count": [P, ctypes.POINTER(I64)],
-                "traknn_knn_scores_static": [P, I64, I64, I, I, I, P, P, P, P],
-                "traknn_stats_read": [P, P, I],
-                "traknn_knn_scores_batched": [P, P, I, I64, P],
-                "traknn_set_grid_weights": [P, P, I64],
-                "traknn_knn_scores_multi": [P, P, I, I64, P],
-                "traknn_knn_stats": [P, P, I64, I, P, I, P, P],
-                "traknn_partition": [I64, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64)],
-                "traknn_knn_partial": [P, P, I64, I64, I, I, I, I, I, P, P, P],
-                "traknn_merge_partials": [P, P, P, I, I64, I, P, P, P, P],
-            }
-            for name, args in sig.items():
-                f = getattr(L, name)
-                f.argtypes = args
-                f.restype = ctypes.c_int
-            L.traknn_status_string.argtypes = [I]
-            L.traknn_status_string.restype = ctypes.c_char_p
-            _lib = L
+            _lib = bind(LIB_PATH)
     return _lib
+
+
+def bind(path: str):
+    """Load a build of the library at `path` with the C signatures of traknn.h (the
+    debug variant libtraknn_bounds.so is loaded this way by its tests)."""
+    L = ctypes.CDLL(path)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "traknn_create": [ctypes.POINTER(P), I],
+        "traknn_destroy": [P],
+        "traknn_set_option": [P, I, I64],
+        "traknn_check_problem": [I64, I64, I, I, I],
+        "traknn_knn_scores": [P, P, I64, I64, I, I, I, P, P, P, P],
+        "traknn_knn_scores_host": [P, P, I64, I64, I, I, I, P, P, P, P],
+        "traknn_score_backward": [P, P, I64, I64, I, I, P, P, P, P],
+        "traknn_sync_status": [P, P],
+        "traknn_profile_read": [P, P, I, ctypes.POINTER(I)],
+        "traknn_launch_count": [P, ctypes.POINTER(I64)],
+        "traknn_knn_scores_static": [P, I64, I64, I, I, I, P, P, P, P],
+        "traknn_stats_read": [P, P, I],
+        "traknn_knn_scores_batched": [P, P, I, I64, P],
+        "traknn_set_grid_weights": [P, P, I64],
+        "traknn_knn_scores_multi": [P, P, I, I64, P],
+        "traknn_knn_stats": [P, P, I64, I, P, I, P, P],
+        "traknn_partition": [I64, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "traknn_knn_partial": [P, P, I64, I64, I, I, I, I, I, P, P, P],
+        "traknn_merge_partials": [P, P, P, I, I64, I, P, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.traknn_status_string.argtypes = [I]
+    L.traknn_status_string.restype = ctypes.c_char_p
+    return L
 
 
 def header_functions(path: str = HEADER_PATH):

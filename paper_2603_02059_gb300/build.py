@@ -1,4 +1,9 @@
-"""Compile libtraknn.so in-tree for sm_103a (nvcc, one -gencode, units in parallel)."""
+"""Compile libtraknn.so in-tree for sm_103a (nvcc, one -gencode, units in parallel).
+
+build(bounds_check=True) compiles the debug variant libtraknn_bounds.so (its own
+object folder): every guarded device-side index is checked against its buffer, and
+a bad one is reported as TRAKNN_ERR_BOUNDS by traknn_sync_status instead of being
+used."""
 from __future__ import annotations
 
 import concurrent.futures
@@ -10,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libtraknn.so")
+BOUNDS_LIB_PATH = os.path.join(HERE, "libtraknn_bounds.so")
 ROOT = os.path.dirname(HERE)
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -33,17 +39,22 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Build (if stale) and return the path of libtraknn.so."""
+def build(force: bool = False, verbose: bool = False, extra_flags=None,
+          bounds_check: bool = False) -> str:
+    """Build (if stale) and return the path of libtraknn.so (or, with bounds_check,
+    of the debug variant libtraknn_bounds.so)."""
     deps = _deps()
-    if not force and not _stale(LIB_PATH, deps):
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    lib_path = BOUNDS_LIB_PATH if bounds_check else LIB_PATH
+    build_dir = BUILD_DIR + ("_bounds" if bounds_check else "")
+    if not force and not _stale(lib_path, deps):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DTRAKNN_BOUNDS_CHECK"] if bounds_check
+                                                     else [])
     headers = [d for d in deps if not d.endswith(".cu")]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         if force or _stale(obj, [src] + headers):
             cmd = [NVCC] + flags + ["-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,13 +66,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=8) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [NVCC, "-shared", "-o", tmp] + objs + ["-cudart=static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

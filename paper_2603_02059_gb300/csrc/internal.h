@@ -27,6 +27,22 @@ constexpr int kErrTimeout = 5;
 constexpr int kErrInvalidArg = 1;
 // Column-mean partial sums use this many row slices (fixed order => deterministic).
 constexpr int kMeanSlices = 64;
+// Status word value of the debug build's index checks (TRAKNN_ERR_BOUNDS).
+constexpr int kErrBounds = 9;
+
+// Index check of the debug build (compiled with -DTRAKNN_BOUNDS_CHECK): an index i
+// outside [0, n) records kErrBounds in the status word and the caller skips the
+// access, so a wrong index is reported by traknn_sync_status instead of touching
+// memory it does not own. In the regular build the check compiles to nothing.
+#ifdef TRAKNN_BOUNDS_CHECK
+__device__ __forceinline__ bool tk_in(long long i, long long n, int* err) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(err, 0, kErrBounds);
+  return false;
+}
+#else
+__device__ __forceinline__ bool tk_in(long long, long long, int*) { return true; }
+#endif
 
 // Work decomposition of the M x M trajectory-pair space shared by the fused
 // Gram/top-k kernels and the merge.
@@ -174,9 +190,13 @@ struct TcWork {
   const long long* col_off; // [stacked strips] column-list offset within the series
   const int* slot_lo;       // [stacked strips] first slot written for the strip's rows
   int sym;                  // 1: upper triangle + column side
-  float* col_d;             // [lists][kstride] column-side candidate distances (in row order)
-  int32_t* col_i;           // [lists][kstride] column-side candidate rows
-  int32_t* col_n;           // [lists] number of valid entries of each column list
+  // Column-side candidate lists, one record of col_pitch() ints per list:
+  // [n, unused, row_0, dist_0, row_1, dist_1, ...] (distances as FP32 bit patterns,
+  // entries in row order or, for a full list, the k best), 16-byte aligned, so that
+  // one 16-byte load gives the count and the first entry.
+  int32_t* col_rec;
+  long long col_ints;       // ints of col_rec (index checks of the debug build)
+  long long part_ints;      // entries of each row-side list array (likewise)
   unsigned int* thr;        // [stacked rows] bit patterns of an upper bound of each row's k-th distance
   int* counter;             // next unit to hand out (zero before the launch)
   int write_lists;          // 0: only publish row bounds (band pre-pass)
@@ -186,6 +206,9 @@ struct TcWork {
   // Every other call: 0 and INT_MAX.
   int part_lo, part_hi;
 };
+
+// Ints per column-list record for list pitch kstride (a multiple of 4).
+__host__ __device__ inline int col_pitch(int kstride) { return 4 + 2 * kstride; }
 
 struct TcArgs {
   int Dp;              // padded row pitch of the stacked operand copies

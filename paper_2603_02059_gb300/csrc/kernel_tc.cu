@@ -153,6 +153,7 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, cons
 // A unit with its series' parameters.
 struct UnitSpan {
   int strip, T0, jlo, jhi, ntiles, slot, nser, step;
+  int carry, adv;  // carry: the last L-1 Gram columns pass from tile to tile; adv: tile stride
   int M, L, k, e, R;      // series: trajectories, length, neighbours, exclusion, rows per strip
   int row_base, out_base, slots, strip_base;
   long long part_base, col_base;
@@ -183,11 +184,16 @@ __device__ __forceinline__ bool unit_span(const TcWork& w, const SeriesInfo* sr,
   us.slot = wu.slot;
   us.step = si.step;
   if (us.jlo >= us.jhi) return false;
-  // Gram tiles follow each other without overlap: tile it covers Gram columns
-  // [jlo + 256 it, jlo + 256 (it+1)); the epilogue carries the last L-1 columns of
-  // a tile into the next, so the windows of all output columns [jlo, jhi) are
-  // complete once Gram column jhi + L - 2 is in
-  us.ntiles = (us.jhi - us.jlo + us.L - 1 + BN - 1) / BN;
+  // A unit of one series: Gram tiles follow each other without overlap, tile it
+  // covering Gram columns [jlo + 256 it, jlo + 256 (it+1)); the epilogue carries the
+  // last L-1 columns of a tile into the next, so the windows of all output columns
+  // [jlo, jhi) are complete once Gram column jhi + L - 2 is in. A unit shared by
+  // several series (each restages the chunk buffer with its own L) has no carry: its
+  // tiles overlap by the largest L - 1 and each yields `step` output columns.
+  us.carry = us.nser == 1;
+  us.adv = us.carry ? BN : us.step;
+  us.ntiles = us.carry ? (us.jhi - us.jlo + us.L - 1 + BN - 1) / BN
+                       : (us.jhi - us.jlo + us.step - 1) / us.step;
   return true;
 }
 
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (u >= w.nunits) break;
         if (!unit_span(w, p.sr.s, u, 0, us)) continue;
         for (int it = 0; ok && it < us.ntiles; ++it) {
-          const int c0 = us.row_base + us.jlo + it * BN;
+          const int c0 = us.row_base + us.jlo + it * us.adv;
           const int a0 = us.row_base + us.T0;
           for (int kb = 0; kb < nkb; ++kb) {
             if (!wait_bounded(empty0 + 8u * stage, phase ^ 1u, ctl)) {
@@ -455,6 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     const int et = threadIdx.x - 64;  // 0..127 within the epilogue
     const int bar = 1;                // the epilogue's named barrier
+    const long long cpitch = col_pitch(w.kstride);  // ints per column-list record
     const int cx = ((warp - 2) & 3) * 8 + (lane & 7);      // column-side column of lanes 0..7
     int qs = 0, gch = 0, gt = 0;
     uint32_t qphase = 0;
@@ -592,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int jsym = us.T0 + us.R;  // column side from here on (sym)
         const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
         if (nser > 1 || it == 0) list.reset();
-        const int c0 = us.jlo + it * BN;
+        const int c0 = us.jlo + it * us.adv;
         // W and row bounds of this tile's output columns j = c0 - (L-1) + x (the
         // previous tile's readers passed its last barrier)
         for (int x = et; x < BN; x += kEpiThreads) {
@@ -630,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float* grow = Gbuf + l * LDG;
           // the diagonal carry: the last L-1 Gram columns of the previous chunk (of
           // the previous tile of this unit at ch = 0) start this chunk's windows
-          if (ch > 0 || it > 0)
+          if (ch > 0 || (it > 0 && us.carry))
             for (int c = 0; c < L - 1; ++c) grow[c] = grow[32 + c];
           const float* cs = Csh + ch * 32;
           // Gram values of the chunk (correction added back): staged in shared memory
@@ -671,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int j0 = c0 + ch * 32 - (L - 1);
           // column side of this chunk: output columns j >= jsym inside the unit
           // the first L-1 columns of a unit's first chunk have no carried window
-          const int xfirst = (ch == 0 && it == 0) ? L - 1 : 0;
+          const int xfirst = (ch == 0 && (it == 0 || !us.carry)) ? L - 1 : 0;
           const uint32_t colrange = w.sym ? bit_range(max(jsym, us.jlo) - j0, us.jhi - j0) &
                                                 bit_range(xfirst, 32)
                                           : 0u;
@@ -752,8 +759,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (ne <= us.k) {
               const long long li = cbase + (j0 + x - jsym);
-              w.col_d[li * w.kstride + before] = Gbuf[l * LDG + x];
-              w.col_i[li * w.kstride + before] = us.T0 + l;
+              const long long at = li * cpitch + 2 + 2 * before;
+              if (tk_in(at + 1, w.col_ints, a.err) && tk_in(before, us.k, a.err))
+                *reinterpret_cast<int2*>(w.col_rec + at) =
+                    make_int2(us.T0 + l, __float_as_int(Gbuf[l * LDG + x]));
             }
           }
           if (colrange && lane < 8 && ((colrange >> cx) & 1u)) {
@@ -773,7 +782,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   mx = fmaxf(mx, Gbuf[r * LDG + cx]);
                 }
               }
-              publish_bound(w.thr + us.out_base + j, mx);
+              if (tk_in(us.out_base + j, a.out_rows, a.err))
+                publish_bound(w.thr + us.out_base + j, mx);
             } else if (ne > us.k) {
               // more than k: keep the k best in (distance, row) order; rows arrive in
               // increasing order, so a strict compare keeps the smaller row first
@@ -801,13 +811,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                   Cli[pos * 32 + cx] = us.T0 + r;
                 }
               }
-              for (int pp = 0; pp < us.k; ++pp) {
-                w.col_d[li * w.kstride + pp] = Cld[pp * 32 + cx];
-                w.col_i[li * w.kstride + pp] = Cli[pp * 32 + cx];
-              }
-              publish_bound(w.thr + us.out_base + j, Cld[(us.k - 1) * 32 + cx]);
+              for (int pp = 0; pp < us.k; ++pp)
+                if (tk_in(li * cpitch + 3 + 2 * pp, w.col_ints, a.err))
+                  *reinterpret_cast<int2*>(w.col_rec + li * cpitch + 2 + 2 * pp) =
+                      make_int2(Cli[pp * 32 + cx], __float_as_int(Cld[pp * 32 + cx]));
+              if (tk_in(us.out_base + j, a.out_rows, a.err))
+                publish_bound(w.thr + us.out_base + j, Cld[(us.k - 1) * 32 + cx]);
             }
-            w.col_n[li] = min(ne, us.k);
+            if (tk_in(li * cpitch, w.col_ints, a.err)) w.col_rec[li * cpitch] = min(ne, us.k);
             cnt[3] += ne > 0;
           }
           // the column side read other rows' Gram values: keep them until it is done
@@ -820,7 +831,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (row_ok) {
           const float kth = kth_of(list, us.k);
-          if (kth < thr_row) publish_bound(w.thr + us.out_base + t, kth);
+          if (kth < thr_row && tk_in(us.out_base + t, a.out_rows, a.err))
+            publish_bound(w.thr + us.out_base + t, kth);
         }
         if (row_ok && w.write_lists && (nser > 1 || it == ntiles - 1)) {
           const size_t base =
@@ -828,8 +840,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int pp = 0; pp < K; ++pp) {
             if (pp < us.k) {
-              a.part_d[base + pp] = list.d[pp];
-              a.part_i[base + pp] = list.i[pp];
+              if (tk_in((long long)base + pp, w.part_ints, a.err)) {
+                a.part_d[base + pp] = list.d[pp];
+                a.part_i[base + pp] = list.i[pp];
+              }
             }
           }
         }

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kBuildThreads)
     adj_build_kernel(const int32_t* __restrict__ idx, const float* __restrict__ g, int N, int L,
                      int M, int k, const int* __restrict__ off, const int* __restrict__ rev,
                      const long long* __restrict__ blk_off, int* __restrict__ blk_nnz,
-                     AdjEntry* __restrict__ ent) {
+                     AdjEntry* __restrict__ ent, int* err) {
   __shared__ unsigned long long key[kKeyCap];
   __shared__ int dayoff[kAdjR + 1];  // first position of each day in the block
   __shared__ int soff[kAdjR + kMaxL + 1];  // off[j] for the window days j of the block
@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(kBuildThreads)
   }
   __syncthreads();
   AdjEntry* out = ent + blk_off[blockIdx.x];
+  const long long cap = blk_off[blockIdx.x + 1] - blk_off[blockIdx.x];  // entries of the block
   int nout = 0;
   // incidence q (0 <= q < day_incidences) of day a: its partner and trajectory
   auto incidence = [&](int a, int q, int& b, int& t, int& kind, int& slot) -> bool {
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(kBuildThreads)
       for (int q = tid; q < n; q += kBuildThreads) {
         int b, t, kind, slot;
         const bool ok = incidence(a, q, b, t, kind, slot);
-        out[nout + q] = ok ? AdjEntry{b, d, inv_k2 * g[t], 0} : AdjEntry{a, d, 0.f, 0};
+        if (tk_in(nout + q, cap, err))
+          out[nout + q] = ok ? AdjEntry{b, d, inv_k2 * g[t], 0} : AdjEntry{a, d, 0.f, 0};
       }
       nout += n;
       d = dh;
@@ -310,7 +312,8 @@ __global__ void __launch_bounds__(kBuildThreads)
         const int t = kind ? b - a + t_lo + slot : t_lo + slot;
         w += inv_k2 * g[t];
       }
-      out[u++] = AdjEntry{b, dd, w, 0};
+      if (tk_in(u, cap, err)) out[u] = AdjEntry{b, dd, w, 0};
+      ++u;
     }
     nout += scan[kBuildThreads - 1];
     __syncthreads();  // the key buffer is refilled by the next segment
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(kGatherCols)
     adj_gather_kernel(const float* __restrict__ X, int N, int D,
                       const long long* __restrict__ blk_off, const int* __restrict__ blk_nnz,
                       const AdjEntry* __restrict__ ent, const float* __restrict__ wts,
-                      float* __restrict__ dX) {
+                      float* __restrict__ dX, int* err) {
   extern __shared__ float adj_sm[];
   float(*xa)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm);
   float(*acc)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm + kAdjR * kGatherCols);
@@ -355,7 +358,12 @@ __global__ void __launch_bounds__(kGatherCols)
     for (int q0 = 0; q0 < n; q0 += kGatherCols) {
       const int nq = min(kGatherCols, n - q0);
       __syncthreads();  // the previous chunk's entries have been read
-      if (tid < nq) ebuf[tid] = __ldg(e4 + q0 + tid);
+      if (tid < nq) {
+        int4 e = __ldg(e4 + q0 + tid);
+        // debug build: an entry's day and partner must be in range (else it adds 0)
+        if (!tk_in(e.y, nd, err) || !tk_in(e.x, N, err)) e = make_int4(a0, 0, 0, 0);
+        ebuf[tid] = e;
+      }
       __syncthreads();
       constexpr int U = 16;
       int q = 0;
@@ -436,14 +444,15 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, N, L, M, k, rev);
   adj_block_scan_kernel<<<1, 1024, 0, st>>>(off, N, L, M, k, nblk, blk_off);
   adj_build_kernel<<<nblk, kBuildThreads, 0, st>>>(idx, g, N, L, M, k, off, rev, blk_off,
-                                                    blk_nnz, ent);
+                                                    blk_nnz, ent, err);
   const size_t smem = 2 * (size_t)kAdjR * kGatherCols * sizeof(float) + kGatherCols * 16;
   e = cudaFuncSetAttribute(adj_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles = (D + kGatherCols - 1) / kGatherCols;
   const dim3 grid(nblk, tiles < 65535 ? tiles : 65535);
-  adj_gather_kernel<<<grid, kGatherCols, smem, st>>>(X, N, D, blk_off, blk_nnz, ent, wts, dX);
+  adj_gather_kernel<<<grid, kGatherCols, smem, st>>>(X, N, D, blk_off, blk_nnz, ent, wts, dX,
+                                                      err);
   *launches += 7;
   return cudaGetLastError();
 }

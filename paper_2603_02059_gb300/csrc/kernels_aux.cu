@@ -15,19 +15,31 @@
 namespace traknn {
 namespace {
 
-// Column sums over fixed row slices (fixed summation order: deterministic).
+// The centring offset only has to be one fixed field subtracted from every day (any
+// value keeps Eq. 2 exact); the mean over days 0, s, 2s, ... (at most kMeanDays of
+// them) is close enough to the full mean to shrink the Gram values as well, and costs
+// a small fraction of a pass over X.
+constexpr int kMeanDays = 4096;
+__host__ __device__ inline int mean_stride(int N) { return (N + kMeanDays - 1) / kMeanDays; }
+__host__ __device__ inline int mean_days(int N) {
+  const int s = mean_stride(N);
+  return (N + s - 1) / s;
+}
+
+// Column sums of the sampled days over fixed slices (fixed summation order:
+// deterministic).
 __global__ void col_partial_kernel(const float* __restrict__ X, int N, int D, float* partial) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D) return;
-  const int per = (N + kMeanSlices - 1) / kMeanSlices;
-  const int r0 = blockIdx.y * per, r1 = min(N, r0 + per);
+  const int stride = mean_stride(N), ns = mean_days(N);
+  const int per = (ns + kMeanSlices - 1) / kMeanSlices;
+  const int r0 = blockIdx.y * per, r1 = min(ns, r0 + per);
   float acc = 0.f;
-  for (int a = r0; a < r1; ++a) acc += X[(size_t)a * D + p];
+  for (int i = r0; i < r1; ++i) acc += X[(size_t)i * stride * D + p];
   partial[(size_t)blockIdx.y * D + p] = acc;
 }
 
-// The centring offset only needs to be one fixed field subtracted from every
-// day (any value keeps Eq. 2 exact), so FP32 sums suffice here.
+// FP32 sums suffice for the offset (see above).
 __global__ void col_final_kernel(const float* __restrict__ partial, int N, int D, float* mu,
                                  int center) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,7 +50,7 @@ __global__ void col_final_kernel(const float* __restrict__ partial, int N, int D
   }
   float acc = 0.f;
   for (int s = 0; s < kMeanSlices; ++s) acc += partial[(size_t)s * D + p];
-  mu[p] = acc / (float)N;
+  mu[p] = acc / (float)mean_days(N);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -85,16 +97,17 @@ __device__ __forceinline__ int find_series(const SeriesInfo* sr, int ns, int r, 
   return lo;
 }
 
-// Column sums of every series over fixed row slices (grid.z = series).
+// Column sums of every series' sampled days over fixed slices (grid.z = series).
 __global__ void col_partial_series_kernel(const __grid_constant__ SeriesTable st, int D,
                                           float* partial) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D) return;
   const SeriesInfo& si = st.s[blockIdx.z];
-  const int per = (si.N + kMeanSlices - 1) / kMeanSlices;
-  const int r0 = blockIdx.y * per, r1 = min(si.N, r0 + per);
+  const int stride = mean_stride(si.N), ns = mean_days(si.N);
+  const int per = (ns + kMeanSlices - 1) / kMeanSlices;
+  const int r0 = blockIdx.y * per, r1 = min(ns, r0 + per);
   float acc = 0.f;
-  for (int a = r0; a < r1; ++a) acc += si.X[(size_t)a * D + p];
+  for (int i = r0; i < r1; ++i) acc += si.X[(size_t)i * stride * D + p];
   partial[((size_t)blockIdx.z * kMeanSlices + blockIdx.y) * D + p] = acc;
 }
 
@@ -109,7 +122,7 @@ __global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
   }
   float acc = 0.f;
   for (int s = 0; s < kMeanSlices; ++s) acc += partial[((size_t)b * kMeanSlices + s) * D + p];
-  mu[(size_t)b * D + p] = acc / (float)st.s[b].N;
+  mu[(size_t)b * D + p] = acc / (float)mean_days(st.s[b].N);
 }
 
 // One warp per stacked day: the centred row x - mu(series) as two BF16 copies hi + lo
@@ -139,9 +152,12 @@ __global__ void __launch_bounds__(256)
                              const float* __restrict__ wts, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
                              float* __restrict__ cval) {
+  // per warp: 32 finished groups of one copy (36-word rows: 16-byte aligned)
+  __shared__ __align__(16) uint32_t stage[8][32 * 36];
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
+  uint32_t* sh = stage[threadIdx.x >> 5];
   const int b = find_series(st.s, st.n, r, false);
   const SeriesInfo& si = st.s[b];
   const int a = r - si.row_base;
@@ -170,13 +186,14 @@ __global__ void __launch_bounds__(256)
   };
   // One read of the row. Lane g0 + lane builds group g0 + lane: its entry pos is grid
   // point pos * groups + g, so for each pos the warp reads 32 consecutive grid points
-  // (coalesced), and each lane writes its group's 64 entries (128 bytes per copy)
-  // with 16-byte stores; entry 63 (the correction) is written once the row's norm is
-  // known. The FP64 norm sums each group's FP32 squares.
+  // (coalesced). The warp's 32 groups (contiguous in the output row) are staged in
+  // shared memory and written with contiguous 16-byte stores; entry 63 (the
+  // correction) is written once the row's norm is known. The FP64 norm sums each
+  // group's FP32 squares.
   double acc = 0.0;
   for (int g0 = 0; g0 < groups; g0 += 32) {
     const int g = g0 + lane;
-    if (g >= groups) break;
+    const int ng = min(32, groups - g0);  // groups of this pass
     uint32_t hv[32], lv[32];  // 64 BF16 entries per copy, in pairs
     float part = 0.f;
 #pragma unroll
@@ -195,13 +212,21 @@ __global__ void __launch_bounds__(256)
       hv[pp] = *reinterpret_cast<const uint32_t*>(&hp);
       lv[pp] = *reinterpret_cast<const uint32_t*>(&lp);
     }
-    acc += (double)part;
-    uint4* hd = reinterpret_cast<uint4*>(h2 + (size_t)g * 32);
-    uint4* ld = reinterpret_cast<uint4*>(l2 + (size_t)g * 32);
+    if (g < groups) acc += (double)part;
+    // hi, then lo: 16-byte chunk c of the pass is chunk c % 8 of group g0 + c / 8
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      hd[v] = make_uint4(hv[4 * v], hv[4 * v + 1], hv[4 * v + 2], hv[4 * v + 3]);
-      ld[v] = make_uint4(lv[4 * v], lv[4 * v + 1], lv[4 * v + 2], lv[4 * v + 3]);
+    for (int copy = 0; copy < 2; ++copy) {
+      const uint32_t* v = copy == 0 ? hv : lv;
+      if (g < groups) {
+        uint4* st4 = reinterpret_cast<uint4*>(sh + lane * 36);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) st4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      __syncwarp();
+      uint4* dst = reinterpret_cast<uint4*>((copy == 0 ? h2 : l2) + (size_t)g0 * 32);
+      for (int c = lane; c < ng * 8; c += 32)
+        dst[c] = *reinterpret_cast<const uint4*>(sh + (c >> 3) * 36 + (c & 7) * 4);
+      __syncwarp();
     }
   }
 #pragma unroll
@@ -356,7 +381,7 @@ __device__ __forceinline__ bool key_less(float d1, int i1, float d2, int i2) {
 // set overflows the buffer, the rounds scan the lists directly.
 __global__ void __launch_bounds__(32 * kMergeWarps)
     merge_tc_kernel(const float* __restrict__ part_d, const int32_t* __restrict__ part_i,
-                    int out_rows, TcWork w, const __grid_constant__ SeriesTable st) {
+                    int out_rows, TcWork w, const __grid_constant__ SeriesTable st, int* err) {
   __shared__ float bd[kMergeWarps][kMergeCap];
   __shared__ int bi[kMergeWarps][kMergeCap];
   __shared__ int bn[kMergeWarps];
@@ -368,6 +393,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
   const int t = r - si.out_base;
   if (t >= si.M) return;
   const int k = si.k, ks = w.kstride;
+  const long long cp = col_pitch(ks);  // ints per column-list record
   const int strip = t / si.rows_out;
   float thr = __uint_as_float(w.thr[r]);
   const int c_lo = w.slot_lo[si.strip_base + strip];
@@ -421,6 +447,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     // lists are read four entries at a time (the list pitch ks is a multiple of 4)
     for (int c = c_lo + lane; c < c_hi; c += 32) {
       const size_t b = (size_t)(plist + c) * ks;
+      if (!tk_in((long long)b + ks - 1, w.part_ints, err)) continue;
       const float4* d4 = reinterpret_cast<const float4*>(part_d + b);
       const int4* i4 = reinterpret_cast<const int4*>(part_i + b);
       bool more = true;
@@ -441,19 +468,32 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
     }
     if (w.sym) {
-      for (int s2 = s2_lo + lane; s2 < s2_hi; s2 += 32) {
-        const long long li = collist(s2);
-        const int nn = w.col_n[li];
-        const float4* d4 = reinterpret_cast<const float4*>(w.col_d + li * ks);
-        const int4* i4 = reinterpret_cast<const int4*>(w.col_i + li * ks);
-        for (int p = 0; p < nn; p += 4) {  // column lists are not sorted
-          const float4 dv = __ldg(d4 + p / 4);
-          const int4 iv = __ldg(i4 + p / 4);
-          const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
-          const int ii[4] = {iv.x, iv.y, iv.z, iv.w};
+      // column lists (not sorted): kColBatch records per lane are requested at once;
+      // the first 16 bytes of a record hold its count and first entry, the next 16
+      // bytes (same 32-byte sector) two more
+      constexpr int kColBatch = 8;
+      for (int sb = s2_lo + lane; sb < s2_hi; sb += 32 * kColBatch) {
+        int4 h0[kColBatch], h1[kColBatch];
+        const int4* rp[kColBatch];
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (p + u < nn && dd[u] <= thr) push(dd[u], ii[u]);
+        for (int u = 0; u < kColBatch; ++u) {
+          const int s2 = sb + 32 * u;
+          rp[u] = s2 < s2_hi && tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)
+                      ? reinterpret_cast<const int4*>(w.col_rec + collist(s2) * cp)
+                      : nullptr;
+          h0[u] = rp[u] ? __ldg(rp[u]) : make_int4(0, 0, 0, 0);
+          h1[u] = rp[u] ? __ldg(rp[u] + 1) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kColBatch; ++u) {
+          const int nn = tk_in(h0[u].x, ks + 1, err) ? h0[u].x : 0;  // count <= k
+          if (nn > 0 && __int_as_float(h0[u].w) <= thr) push(__int_as_float(h0[u].w), h0[u].z);
+          if (nn > 1 && __int_as_float(h1[u].y) <= thr) push(__int_as_float(h1[u].y), h1[u].x);
+          if (nn > 2 && __int_as_float(h1[u].w) <= thr) push(__int_as_float(h1[u].w), h1[u].z);
+          for (int p = 3; p < nn; ++p) {
+            const int2 e = __ldg(reinterpret_cast<const int2*>(rp[u]) + 1 + p);
+            if (__int_as_float(e.y) <= thr) push(__int_as_float(e.y), e.x);
+          }
         }
       }
     }
@@ -485,6 +525,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     } else {
       for (int c = c_lo + lane; c < c_hi; c += 32) {
         const size_t b = (size_t)(plist + c) * ks;
+        if (!tk_in((long long)b + ks - 1, w.part_ints, err)) continue;
         for (int p = 0; p < k; ++p) {
           const int ii = part_i[b + p];
           if (ii < 0 || part_d[b + p] > thr) break;
@@ -493,10 +534,12 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
       if (w.sym) {
         for (int s2 = s2_lo + lane; s2 < s2_hi; s2 += 32) {
-          const long long li = collist(s2);
-          const int nn = w.col_n[li];
+          if (!tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)) continue;
+          const int2* rec = reinterpret_cast<const int2*>(w.col_rec + collist(s2) * cp);
+          const int nn = tk_in(rec[0].x, ks + 1, err) ? rec[0].x : 0;
           for (int p = 0; p < nn; ++p) {
-            if (w.col_d[li * ks + p] <= thr) consider(w.col_d[li * ks + p], w.col_i[li * ks + p]);
+            const int2 e = rec[1 + p];
+            if (__int_as_float(e.y) <= thr) consider(__int_as_float(e.y), e.x);
           }
         }
       }
@@ -526,7 +569,8 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
 cudaError_t launch_merge_tc(const TcArgs& a, const TcWork& w, const SeriesTable& sr,
                             cudaStream_t st) {
   const int blocks = (a.out_rows + kMergeWarps - 1) / kMergeWarps;
-  merge_tc_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(a.part_d, a.part_i, a.out_rows, w, sr);
+  merge_tc_kernel<<<blocks, 32 * kMergeWarps, 0, st>>>(a.part_d, a.part_i, a.out_rows, w, sr,
+                                                        a.err);
   return cudaGetLastError();
 }
 

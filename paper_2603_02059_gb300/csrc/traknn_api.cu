@@ -270,9 +270,7 @@ struct TcBuffers {
   float* part_d;
   int32_t* part_i;
   unsigned int* thr;
-  int32_t* col_n;
-  float* col_d;
-  int32_t* col_i;
+  int32_t* col_rec;
   int* counter;
   float* scratch;
   float* pscore;  // [out_rows] scores of partial lists (split series), not returned
@@ -302,9 +300,8 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
   b.part_d = reinterpret_cast<float*>(take((size_t)p.part_lists * ks * sizeof(float)));
   b.part_i = reinterpret_cast<int32_t*>(take((size_t)p.part_lists * ks * sizeof(int32_t)));
   b.thr = reinterpret_cast<unsigned int*>(take((size_t)p.out_rows * sizeof(unsigned int)));
-  b.col_n = reinterpret_cast<int32_t*>(take((size_t)p.col_lists * sizeof(int32_t)));
-  b.col_d = reinterpret_cast<float*>(take((size_t)p.col_lists * ks * sizeof(float)));
-  b.col_i = reinterpret_cast<int32_t*>(take((size_t)p.col_lists * ks * sizeof(int32_t)));
+  b.col_rec = reinterpret_cast<int32_t*>(
+      take((size_t)p.col_lists * col_pitch((int)ks) * sizeof(int32_t)));
   b.counter = reinterpret_cast<int*>(take(256));
   b.scratch = reinterpret_cast<float*>(take(tc_scratch_bytes(num_ctas)));
   b.pscore = reinterpret_cast<float*>(take((size_t)p.out_rows * sizeof(float)));
@@ -393,9 +390,9 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   w.col_off = reinterpret_cast<const long long*>(pd + ub);
   w.slot_lo = reinterpret_cast<const int*>(pd + ub + cb);
   w.sym = h->sym;
-  w.col_d = b.col_d;
-  w.col_i = b.col_i;
-  w.col_n = b.col_n;
+  w.col_rec = b.col_rec;
+  w.col_ints = p.col_lists * col_pitch(w.kstride);
+  w.part_ints = p.part_lists * w.kstride;
   w.thr = b.thr;
   w.counter = b.counter;
   w.write_lists = 1;
@@ -575,6 +572,7 @@ const char* traknn_status_string(traknn_status s) {
     case TRAKNN_ERR_UNSUPPORTED_DEVICE: return "device is not sm_103";
     case TRAKNN_ERR_UNSUPPORTED: return "L or k above the compiled limits";
     case TRAKNN_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch array of the static entry point";
+    case TRAKNN_ERR_BOUNDS: return "a device-side index check failed (debug build)";
   }
   return "unknown status";
 }

@@ -17,7 +17,7 @@ def test_library_exports_every_declared_function():
 
 def test_status_strings():
     lib = tk.lib()
-    for code in range(9):
+    for code in range(10):
         s = lib.traknn_status_string(code)
         assert isinstance(s, bytes) and len(s) > 0
     assert lib.traknn_status_string(0) == b"ok"
