@@ -299,11 +299,14 @@ inline void split_strips(long long M, int L, int nparts, int part, int* s_lo, in
 }
 // emb > 1: each operand row is the emb-day trajectory starting at that day (emb * D
 // values, contiguous in X); the series table then describes trajectories (N = M, L = 1).
+// Rows [r_lo, rows) of the stacked operands (all rows with r_lo = 0).
 cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int emb, int groups,
                                      bool correct, const float* mu, const float* wts, void* hi,
-                                     void* lo, double* norms, float* cval, cudaStream_t st);
+                                     void* lo, double* norms, float* cval, cudaStream_t st,
+                                     int r_lo = 0);
+// Window sums of the stacked trajectory rows [r_lo, out_rows).
 cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
-                                 float* W, cudaStream_t st);
+                                 float* W, cudaStream_t st, int r_lo = 0);
 cudaError_t launch_merge(const FusedArgs& a, int32_t* idx, float* dist, float* score,
                          cudaStream_t st);
 // Exact top-k of the union of nparts sorted candidate lists per row ([nparts][M][k],

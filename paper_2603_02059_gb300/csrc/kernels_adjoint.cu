@@ -96,14 +96,10 @@ constexpr int kKeyCap = 4096;     // incidences sorted at once in shared memory
 constexpr int kBuildThreads = 256;
 constexpr int kGatherCols = 256;  // grid points per gather CTA (one per thread)
 
-// One merged entry of a block's gradient list: partner day b, output day a0 + d,
-// summed weight w (16 bytes, read as one vector).
-struct AdjEntry {
-  int b;
-  int d;
-  float w;
-  int pad;
-};
+// One merged entry of a block's gradient list: partner day b and summed weight w
+// (as FP32 bits). A block's entries are in order of output day (blk_day gives each
+// day's first entry), then partner.
+typedef int2 AdjEntry;
 
 // Incidences of day a: the forward ones (k per trajectory t of its window) and the
 // reverse segments of the days j of its window, [max(0, a-L+1), min(a, M-1)].
@@ -169,18 +165,20 @@ __global__ void adj_block_scan_kernel(const int* __restrict__ off, int N, int L,
 
 // The merged entry list of one block of kAdjR days (one CTA per block). The days are
 // cut into segments of consecutive days whose incidences fit the key buffer. A
-// segment's keys are (partner b << 32) | (day d << 24) | (kind << 23) | slot: kind 0 is
-// a forward incidence (trajectory t = t_lo + slot of day a0 + d), kind 1 a reverse one
-// (window day j = t_lo + slot, trajectory t = b - a + j). Every key is unique, so the
-// sorted order is fixed whatever order the reverse lists were filled in; each run of
-// equal (b, d) becomes one entry whose weight is summed in key order.
+// segment's keys are (day d << 58) | (partner b << 24) | (kind << 23) | slot: kind 0
+// is a forward incidence (trajectory t = t_lo + slot of day a0 + d), kind 1 a reverse
+// one (window day j = t_lo + slot, trajectory t = b - a + j). Every key is unique, so
+// the sorted order is fixed whatever order the reverse lists were filled in; each run
+// of equal (d, b) becomes one entry whose weight is summed in key order. blk_day
+// receives the first entry of every day (kAdjR + 1 offsets per block).
 __global__ void __launch_bounds__(kBuildThreads)
     adj_build_kernel(const int32_t* __restrict__ idx, const float* __restrict__ g, int N, int L,
                      int M, int k, const int* __restrict__ off, const int* __restrict__ rev,
-                     const long long* __restrict__ blk_off, int* __restrict__ blk_nnz,
+                     const long long* __restrict__ blk_off, int* __restrict__ blk_day,
                      AdjEntry* __restrict__ ent, int* err) {
   __shared__ unsigned long long key[kKeyCap];
   __shared__ int dayoff[kAdjR + 1];  // first position of each day in the block
+  __shared__ int daycnt[kAdjR];      // entries written for each day
   __shared__ int soff[kAdjR + kMaxL + 1];  // off[j] for the window days j of the block
   __shared__ int scan[kBuildThreads];
   const int tid = threadIdx.x;
@@ -190,6 +188,7 @@ __global__ void __launch_bounds__(kBuildThreads)
   // window days of the block's days: [jb, je]; their reverse-list offsets off[jb..je+1]
   const int jb = max(0, a0 - L + 1), je = min(a0 + nd - 1, M - 1);
   for (int i = tid; i <= je - jb + 1; i += kBuildThreads) soff[i] = off[jb + i];
+  if (tid < kAdjR) daycnt[tid] = 0;
   __syncthreads();
   auto offj = [&](int j) { return soff[j - jb]; };  // off[j], jb <= j <= je + 1
   if (tid == 0) {
@@ -241,8 +240,9 @@ __global__ void __launch_bounds__(kBuildThreads)
         int b, t, kind, slot;
         const bool ok = incidence(a, q, b, t, kind, slot);
         if (tk_in(nout + q, cap, err))
-          out[nout + q] = ok ? AdjEntry{b, d, inv_k2 * g[t], 0} : AdjEntry{a, d, 0.f, 0};
+          out[nout + q] = ok ? make_int2(b, __float_as_int(inv_k2 * g[t])) : make_int2(a, 0);
       }
+      if (tid == 0) daycnt[d] = n;
       nout += n;
       d = dh;
       continue;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kBuildThreads)
         while (dayoff[dd + 1] <= base + q) ++dd;
         int b, t, kind, slot;
         if (incidence(a0 + dd, base + q - dayoff[dd], b, t, kind, slot))
-          kq = ((unsigned long long)(unsigned)b << 32) | ((unsigned long long)dd << 24) |
+          kq = ((unsigned long long)dd << 58) | ((unsigned long long)(unsigned)b << 24) |
                ((unsigned long long)kind << 23) | (unsigned long long)slot;
       }
       key[q] = kq;
@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(kBuildThreads)
       const int q = q0 + i;
       if (!head(q)) continue;
       const unsigned long long run = key[q] >> 24;
-      const int b = (int)(key[q] >> 32);
-      const int dd = (int)((key[q] >> 24) & 0xFF);
+      const int b = (int)((key[q] >> 24) & 0x3FFFFFFFull);
+      const int dd = (int)(key[q] >> 58);
       const int a = a0 + dd;
       const int t_lo = max(0, a - L + 1);
       float w = 0.f;
@@ -312,82 +312,81 @@ __global__ void __launch_bounds__(kBuildThreads)
         const int t = kind ? b - a + t_lo + slot : t_lo + slot;
         w += inv_k2 * g[t];
       }
-      if (tk_in(u, cap, err)) out[u] = AdjEntry{b, dd, w, 0};
+      if (tk_in(u, cap, err)) out[u] = make_int2(b, __float_as_int(w));
       ++u;
+      atomicAdd(&daycnt[dd], 1);
     }
     nout += scan[kBuildThreads - 1];
     __syncthreads();  // the key buffer is refilled by the next segment
     d = dh;
   }
-  if (tid == 0) blk_nnz[blockIdx.x] = nout;
+  __syncthreads();
+  if (tid == 0) {
+    int pos = 0;
+    for (int dd = 0; dd < kAdjR; ++dd) {
+      blk_day[blockIdx.x * (kAdjR + 1) + dd] = pos;
+      pos += dd < nd ? daycnt[dd] : 0;
+    }
+    blk_day[blockIdx.x * (kAdjR + 1) + kAdjR] = pos;
+  }
 }
 
-// dX for one block of kAdjR days and kGatherCols grid points: every entry (b, d, w) of
-// the block's list adds w (X[a0+d] - X[b]) to day a0 + d, in list order. Each thread
-// owns one grid point, so its rows of X[a0 ..] and of the sums live in shared memory
-// columns that no other thread touches. blockIdx.x is the day block and blockIdx.y
-// the grid-point tile: CTAs are scheduled with x fastest, so the CTAs running at one
-// time share a tile of X, which stays in L2 while the entries re-read its rows.
-__global__ void __launch_bounds__(kGatherCols)
+// dX for one block of kAdjR days and kGatherCols grid points: for each day a0 + d,
+// every entry (b, w) of the day adds w (X[a0+d] - X[b]), in list order. Each thread
+// owns one grid point and keeps the block's kAdjR values of X and sums in registers;
+// the entries (the same for every thread) are read through L1, partner values kU at a
+// time so that kU loads per thread are in flight. blockIdx.x is the day block and
+// blockIdx.y the grid-point tile: CTAs are scheduled with x fastest, so the CTAs
+// running at one time share a tile of X, which stays in L2 while the entries re-read
+// its rows (consecutive days of a block share many partner rows, which then come
+// from L1).
+constexpr int kU = 8;
+__global__ void __launch_bounds__(kGatherCols, 2)
     adj_gather_kernel(const float* __restrict__ X, int N, int D,
-                      const long long* __restrict__ blk_off, const int* __restrict__ blk_nnz,
+                      const long long* __restrict__ blk_off, const int* __restrict__ blk_day,
                       const AdjEntry* __restrict__ ent, const float* __restrict__ wts,
                       float* __restrict__ dX, int* err) {
-  extern __shared__ float adj_sm[];
-  float(*xa)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm);
-  float(*acc)[kGatherCols] = reinterpret_cast<float(*)[kGatherCols]>(adj_sm + kAdjR * kGatherCols);
-  int4* ebuf = reinterpret_cast<int4*>(adj_sm + 2 * kAdjR * kGatherCols);  // [kGatherCols]
+  __shared__ int sday[kAdjR + 1];
   const int tid = threadIdx.x;
   const int a0 = blockIdx.x * kAdjR;
   const int nd = min(kAdjR, N - a0);
-  const int4* e4 = reinterpret_cast<const int4*>(ent + blk_off[blockIdx.x]);
-  const int n = blk_nnz[blockIdx.x];
+  const AdjEntry* e2 = ent + blk_off[blockIdx.x];
+  if (tid <= kAdjR) sday[tid] = blk_day[blockIdx.x * (kAdjR + 1) + tid];
+  __syncthreads();
   const int tiles = (D + kGatherCols - 1) / kGatherCols;
   for (int tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
     const int p = tile * kGatherCols + tid;
     const bool pin = p < D;
-#pragma unroll 4
-    for (int d = 0; d < kAdjR; ++d) {
-      xa[d][tid] = (pin && d < nd) ? __ldg(X + (size_t)(a0 + d) * D + p) : 0.f;
-      acc[d][tid] = 0.f;
-    }
     const float* xp = X + (pin ? p : 0);
-    // entries are staged kGatherCols at a time (one coalesced load per thread) and
-    // then read from shared memory by every thread; partner values are loaded U at
-    // a time so that U loads per thread are in flight
-    for (int q0 = 0; q0 < n; q0 += kGatherCols) {
-      const int nq = min(kGatherCols, n - q0);
-      __syncthreads();  // the previous chunk's entries have been read
-      if (tid < nq) {
-        int4 e = __ldg(e4 + q0 + tid);
-        // debug build: an entry's day and partner must be in range (else it adds 0)
-        if (!tk_in(e.y, nd, err) || !tk_in(e.x, N, err)) e = make_int4(a0, 0, 0, 0);
-        ebuf[tid] = e;
-      }
-      __syncthreads();
-      constexpr int U = 16;
-      int q = 0;
-      for (; q + U <= nq; q += U) {
-        float xb[U];
+    float xa[kAdjR], acc[kAdjR];
 #pragma unroll
-        for (int u = 0; u < U; ++u) xb[u] = pin ? __ldg(xp + (size_t)ebuf[q + u].x * D) : 0.f;
+    for (int d = 0; d < kAdjR; ++d) {
+      xa[d] = (pin && d < nd) ? __ldg(xp + (size_t)(a0 + d) * D) : 0.f;
+      acc[d] = 0.f;
+    }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int4 e = ebuf[q + u];
-          acc[e.y][tid] = fmaf(__int_as_float(e.z), xa[e.y][tid] - xb[u], acc[e.y][tid]);
+    for (int d = 0; d < kAdjR; ++d) {
+      const int q1 = sday[d + 1];
+      for (int q = sday[d]; q < q1; q += kU) {
+        AdjEntry e[kU];
+        float xb[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          // past the day's last entry: weight 0 against the day itself
+          e[u] = q + u < q1 ? __ldg(e2 + q + u) : make_int2(a0 + d, 0);
+          if (!tk_in(e[u].x, N, err)) e[u] = make_int2(a0 + d, 0);
         }
-      }
-      for (; q < nq; ++q) {
-        const int4 e = ebuf[q];
-        const float xb = pin ? __ldg(xp + (size_t)e.x * D) : 0.f;
-        acc[e.y][tid] = fmaf(__int_as_float(e.z), xa[e.y][tid] - xb, acc[e.y][tid]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) xb[u] = pin ? __ldg(xp + (size_t)e[u].x * D) : 0.f;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) acc[d] = fmaf(__int_as_float(e[u].y), xa[d] - xb[u], acc[d]);
       }
     }
     if (pin) {
       const float wp = wts ? wts[p] : 1.f;
-#pragma unroll 4
-      for (int d = 0; d < nd; ++d)
-        dX[(size_t)(a0 + d) * D + p] = wts ? acc[d][tid] * wp : acc[d][tid];
+#pragma unroll
+      for (int d = 0; d < kAdjR; ++d)
+        if (d < nd) dX[(size_t)(a0 + d) * D + p] = wts ? acc[d] * wp : acc[d];
     }
   }
 }
@@ -401,7 +400,7 @@ inline size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 // Workspace layout: merged entries (at most one per incidence, 2 L k M in all), block
 // offsets and counts, then the reverse neighbour index (count, cursor, off, rev).
 struct AdjLayout {
-  size_t ent, blk_off, blk_nnz, count, total;
+  size_t ent, blk_off, blk_day, count, total;
 };
 
 AdjLayout adj_layout(int N, int L, int k) {
@@ -410,8 +409,8 @@ AdjLayout adj_layout(int N, int L, int k) {
   AdjLayout l;
   l.ent = 0;
   l.blk_off = up256(2 * (size_t)L * k * M * sizeof(AdjEntry));
-  l.blk_nnz = l.blk_off + up256((nblk + 1) * sizeof(long long));
-  l.count = l.blk_nnz + up256(nblk * sizeof(int));
+  l.blk_day = l.blk_off + up256((nblk + 1) * sizeof(long long));
+  l.count = l.blk_day + up256(nblk * (kAdjR + 1) * sizeof(int));
   l.total = l.count + up256((3 * M + 1 + M * (size_t)k) * sizeof(int));
   return l;
 }
@@ -428,7 +427,7 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   char* base = static_cast<char*>(ws);
   AdjEntry* ent = reinterpret_cast<AdjEntry*>(base + lay.ent);
   long long* blk_off = reinterpret_cast<long long*>(base + lay.blk_off);
-  int* blk_nnz = reinterpret_cast<int*>(base + lay.blk_nnz);
+  int* blk_day = reinterpret_cast<int*>(base + lay.blk_day);
   int* count = reinterpret_cast<int*>(base + lay.count);
   int* cursor = count + M;
   int* off = cursor + M;
@@ -444,15 +443,10 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_sort_kernel<<<(M + 127) / 128, 128, 0, st>>>(off, N, L, M, k, rev);
   adj_block_scan_kernel<<<1, 1024, 0, st>>>(off, N, L, M, k, nblk, blk_off);
   adj_build_kernel<<<nblk, kBuildThreads, 0, st>>>(idx, g, N, L, M, k, off, rev, blk_off,
-                                                    blk_nnz, ent, err);
-  const size_t smem = 2 * (size_t)kAdjR * kGatherCols * sizeof(float) + kGatherCols * 16;
-  e = cudaFuncSetAttribute(adj_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
+                                                    blk_day, ent, err);
   const int tiles = (D + kGatherCols - 1) / kGatherCols;
   const dim3 grid(nblk, tiles < 65535 ? tiles : 65535);
-  adj_gather_kernel<<<grid, kGatherCols, smem, st>>>(X, N, D, blk_off, blk_nnz, ent, wts, dX,
-                                                      err);
+  adj_gather_kernel<<<grid, kGatherCols, 0, st>>>(X, N, D, blk_off, blk_day, ent, wts, dX, err);
   *launches += 7;
   return cudaGetLastError();
 }

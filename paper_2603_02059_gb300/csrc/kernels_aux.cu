@@ -147,14 +147,14 @@ __global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
 // and the norm of a row is the window sum of the day norms.
 template <bool kCorr>
 __global__ void __launch_bounds__(256)
-    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int rows, int D, int emb,
-                             int groups, const float* __restrict__ mu,
+    prep_split_series_kernel(const __grid_constant__ SeriesTable st, int r_lo, int rows, int D,
+                             int emb, int groups, const float* __restrict__ mu,
                              const float* __restrict__ wts, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
                              float* __restrict__ cval) {
   // per warp: 32 finished groups of one copy (36-word rows: 16-byte aligned)
   __shared__ __align__(16) uint32_t stage[8][32 * 36];
-  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int r = r_lo + blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   uint32_t* sh = stage[threadIdx.x >> 5];
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // W of every stacked trajectory row: an explicit L-term FP64 sum of its series' norms.
-__global__ void window_series_kernel(const __grid_constant__ SeriesTable st, int out_rows,
-                                     const double* __restrict__ norms, float* W) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void window_series_kernel(const __grid_constant__ SeriesTable st, int r_lo,
+                                     int out_rows, const double* __restrict__ norms, float* W) {
+  const int r = r_lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= out_rows) return;
   const int b = find_series(st.s, st.n, r, true);
   const SeriesInfo& si = st.s[b];
@@ -597,22 +597,26 @@ cudaError_t launch_col_mean_series(const SeriesTable& sr, int D, float* partial,
 
 cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int emb, int groups,
                                      bool correct, const float* mu, const float* wts, void* hi,
-                                     void* lo, double* norms, float* cval, cudaStream_t st) {
-  const int blocks = (rows + 7) / 8;
+                                     void* lo, double* norms, float* cval, cudaStream_t st,
+                                     int r_lo) {
+  if (rows <= r_lo) return cudaSuccess;
+  const int blocks = (rows - r_lo + 7) / 8;
   if (correct)
     prep_split_series_kernel<true><<<blocks, 256, 0, st>>>(
-        sr, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
+        sr, r_lo, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
         static_cast<__nv_bfloat16*>(lo), norms, cval);
   else
     prep_split_series_kernel<false><<<blocks, 256, 0, st>>>(
-        sr, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
+        sr, r_lo, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
         static_cast<__nv_bfloat16*>(lo), norms, cval);
   return cudaGetLastError();
 }
 
 cudaError_t launch_window_series(const SeriesTable& sr, int out_rows, const double* norms,
-                                 float* W, cudaStream_t st) {
-  window_series_kernel<<<(out_rows + 255) / 256, 256, 0, st>>>(sr, out_rows, norms, W);
+                                 float* W, cudaStream_t st, int r_lo) {
+  if (out_rows <= r_lo) return cudaSuccess;
+  window_series_kernel<<<(out_rows - r_lo + 255) / 256, 256, 0, st>>>(sr, r_lo, out_rows, norms,
+                                                                     W);
   return cudaGetLastError();
 }
 

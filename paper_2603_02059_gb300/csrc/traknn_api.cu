@@ -40,6 +40,10 @@ struct TcPlan {
   long long part_lists = 0, col_lists = 0;
   int emb = 1;  // days per operand row (trajectory-embedded operands when > 1)
   int part_lo = 0, part_hi = INT_MAX;  // strips evaluated (one part of a split series)
+  // Two phases (host-buffer calls, one series): strips >= phase_strip first (their
+  // main units, then band units, are the first nunits_a / nband_a of each list), so
+  // they can run while the days before phase_strip are still being copied in.
+  int phase_strip = 0, nunits_a = 0, nband_a = 0;
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
@@ -158,11 +162,12 @@ inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
 // unit is one tile long and carries all B series (pad[0] = B), and the first series
 // (smallest L, most trajectories) defines the units' column ranges.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
-                int group_opt, bool shared, int part_lo, int part_hi, TcPlan& p) {
+                int group_opt, bool shared, int part_lo, int part_hi, int phase_strip,
+                TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
-  std::vector<WorkUnit> band;
+  std::vector<WorkUnit> band, later, later_band;  // the second phase's units
   int row_base = 0, out_base = 0, strip_base = 0;
   long long part_base = 0, col_base = 0;
   p.kmax = 0;
@@ -212,15 +217,23 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
             int jlo = c * cols;
             const int jhi = std::min(M, (c + 1) * cols);
             if (sym) jlo = std::max(jlo, s * R);
-            if (jlo < jhi) p.units.push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
+            if (jlo < jhi)
+              (phase_strip > 0 && s < phase_strip ? later : p.units)
+                  .push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
           }
       }
       // band: two tiles of columns (2 kTileCols - (L-1) outputs) centred on the strip's rows
       const int bw = std::max(0, (2 * kTileCols - (Lg - 1) - R) / 2);
       for (int s = std::max(0, part_lo); s < std::min(strips, part_hi); ++s) {
         const int T0 = s * R;
-        const int jlo = std::max(0, T0 - bw), jhi = std::min(M, T0 + R + bw);
-        if (jlo < jhi) band.push_back(WorkUnit{b, s, jlo, jhi, 0, {nser, 0, 0}});
+        int jlo = std::max(0, T0 - bw);
+        const int jhi = std::min(M, T0 + R + bw);
+        // first-phase band units stay clear of the days still being copied (a band
+        // only seeds bounds, from whatever candidates it holds)
+        if (phase_strip > 0 && s >= phase_strip) jlo = std::max(jlo, phase_strip * R);
+        if (jlo < jhi)
+          (phase_strip > 0 && s < phase_strip ? later_band : band)
+              .push_back(WorkUnit{b, s, jlo, jhi, 0, {nser, 0, 0}});
       }
     }
     if (!shared || b == B - 1) row_base += N;
@@ -231,6 +244,11 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     p.kmax = std::max(p.kmax, k);
     p.Lmax = std::max(p.Lmax, L);
   }
+  p.phase_strip = phase_strip;
+  p.nunits_a = (int)p.units.size();
+  p.nband_a = (int)band.size();
+  p.units.insert(p.units.end(), later.begin(), later.end());
+  band.insert(band.end(), later_band.begin(), later_band.end());
   p.nunits = (int)p.units.size();
   p.nband = (int)band.size();
   p.units.insert(p.units.end(), band.begin(), band.end());
@@ -313,17 +331,18 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
 // and size the workspace. Must not run during a stream capture.
 traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
                          bool shared, int emb, cudaStream_t s, TcBuffers* out,
-                         int part_lo = 0, int part_hi = INT_MAX) {
+                         int part_lo = 0, int part_hi = INT_MAX, int phase_strip = 0) {
   std::vector<int64_t> key = shape_key(sd, B, D, h);
   key.push_back(tiles);
   key.push_back(shared ? 1 : 0);
   key.push_back(emb);
   key.push_back(part_lo);
   key.push_back(part_hi);
+  key.push_back(phase_strip);
   TcPlan& p = h->plan;
   if (p.key != key) {
     build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, part_lo, part_hi,
-               p);
+               phase_strip, p);
     p.key = key;
     p.emb = emb;
     p.part_lo = part_lo;
