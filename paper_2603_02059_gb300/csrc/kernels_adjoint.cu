@@ -333,19 +333,22 @@ __global__ void __launch_bounds__(kBuildThreads)
 
 // dX for one block of kAdjR days and kGatherCols grid points: for each day a0 + d,
 // every entry (b, w) of the day adds w (X[a0+d] - X[b]), in list order. Each thread
-// owns one grid point and keeps the block's kAdjR values of X and sums in registers;
-// the entries (the same for every thread) are read through L1, partner values kU at a
-// time so that kU loads per thread are in flight. blockIdx.x is the day block and
-// blockIdx.y the grid-point tile: CTAs are scheduled with x fastest, so the CTAs
-// running at one time share a tile of X, which stays in L2 while the entries re-read
-// its rows (consecutive days of a block share many partner rows, which then come
-// from L1).
-constexpr int kU = 8;
+// owns one grid point and keeps the block's kAdjR values of X and sums in registers.
+// The entries (the same for every thread) are staged in shared memory kStage at a
+// time, and partner values are loaded kU at a time so that kU loads per thread (and
+// about 64 KB per SM) are in flight: the kernel is bound by the latency of these L2
+// reads. blockIdx.x is the day block and blockIdx.y the grid-point tile: CTAs are
+// scheduled with x fastest, so the CTAs running at one time share a tile of X, which
+// stays in L2 while the entries re-read its rows (consecutive days of a block share
+// many partner rows, which then also come from L1).
+constexpr int kU = 32;
+constexpr int kStage = 2048;
 __global__ void __launch_bounds__(kGatherCols, 2)
     adj_gather_kernel(const float* __restrict__ X, int N, int D,
                       const long long* __restrict__ blk_off, const int* __restrict__ blk_day,
                       const AdjEntry* __restrict__ ent, const float* __restrict__ wts,
                       float* __restrict__ dX, int* err) {
+  __shared__ AdjEntry se[kStage];
   __shared__ int sday[kAdjR + 1];
   const int tid = threadIdx.x;
   const int a0 = blockIdx.x * kAdjR;
@@ -353,6 +356,7 @@ __global__ void __launch_bounds__(kGatherCols, 2)
   const AdjEntry* e2 = ent + blk_off[blockIdx.x];
   if (tid <= kAdjR) sday[tid] = blk_day[blockIdx.x * (kAdjR + 1) + tid];
   __syncthreads();
+  const int ntot = sday[kAdjR];
   const int tiles = (D + kGatherCols - 1) / kGatherCols;
   for (int tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
     const int p = tile * kGatherCols + tid;
@@ -364,22 +368,27 @@ __global__ void __launch_bounds__(kGatherCols, 2)
       xa[d] = (pin && d < nd) ? __ldg(xp + (size_t)(a0 + d) * D) : 0.f;
       acc[d] = 0.f;
     }
+    for (int c0 = 0; c0 < ntot; c0 += kStage) {
+      const int c1 = min(ntot, c0 + kStage);
+      __syncthreads();  // the previous pass has read its entries
+      for (int i = tid; i < c1 - c0; i += kGatherCols) {
+        AdjEntry e = __ldg(e2 + c0 + i);
+        if (!tk_in(e.x, N, err)) e = make_int2(a0, 0);  // debug build: adds 0
+        se[i] = e;
+      }
+      __syncthreads();
 #pragma unroll
-    for (int d = 0; d < kAdjR; ++d) {
-      const int q1 = sday[d + 1];
-      for (int q = sday[d]; q < q1; q += kU) {
-        AdjEntry e[kU];
-        float xb[kU];
+      for (int d = 0; d < kAdjR; ++d) {
+        const int q1 = min(sday[d + 1], c1);
+        for (int q = max(sday[d], c0); q < q1; q += kU) {
+          float xb[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          // past the day's last entry: weight 0 against the day itself
-          e[u] = q + u < q1 ? __ldg(e2 + q + u) : make_int2(a0 + d, 0);
-          if (!tk_in(e[u].x, N, err)) e[u] = make_int2(a0 + d, 0);
+          for (int u = 0; u < kU; ++u)
+            xb[u] = (pin && q + u < q1) ? __ldg(xp + (size_t)se[q + u - c0].x * D) : 0.f;
+#pragma unroll
+          for (int u = 0; u < kU; ++u)
+            if (q + u < q1) acc[d] = fmaf(__int_as_float(se[q + u - c0].y), xa[d] - xb[u], acc[d]);
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) xb[u] = pin ? __ldg(xp + (size_t)e[u].x * D) : 0.f;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) acc[d] = fmaf(__int_as_float(e[u].y), xa[d] - xb[u], acc[d]);
       }
     }
     if (pin) {

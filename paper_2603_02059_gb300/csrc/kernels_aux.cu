@@ -19,12 +19,6 @@ namespace {
 // value keeps Eq. 2 exact); the mean over days 0, s, 2s, ... (at most kMeanDays of
 // them) is close enough to the full mean to shrink the Gram values as well, and costs
 // a small fraction of a pass over X.
-constexpr int kMeanDays = 4096;
-__host__ __device__ inline int mean_stride(int N) { return (N + kMeanDays - 1) / kMeanDays; }
-__host__ __device__ inline int mean_days(int N) {
-  const int s = mean_stride(N);
-  return (N + s - 1) / s;
-}
 
 // Column sums of the sampled days over fixed slices (fixed summation order:
 // deterministic).
@@ -152,12 +146,9 @@ __global__ void __launch_bounds__(256)
                              const float* __restrict__ wts, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
                              float* __restrict__ cval) {
-  // per warp: 32 finished groups of one copy (36-word rows: 16-byte aligned)
-  __shared__ __align__(16) uint32_t stage[8][32 * 36];
   const int r = r_lo + blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
-  uint32_t* sh = stage[threadIdx.x >> 5];
   const int b = find_series(st.s, st.n, r, false);
   const SeriesInfo& si = st.s[b];
   const int a = r - si.row_base;
@@ -186,14 +177,13 @@ __global__ void __launch_bounds__(256)
   };
   // One read of the row. Lane g0 + lane builds group g0 + lane: its entry pos is grid
   // point pos * groups + g, so for each pos the warp reads 32 consecutive grid points
-  // (coalesced). The warp's 32 groups (contiguous in the output row) are staged in
-  // shared memory and written with contiguous 16-byte stores; entry 63 (the
-  // correction) is written once the row's norm is known. The FP64 norm sums each
-  // group's FP32 squares.
+  // (coalesced), and each lane writes its group's 64 entries (128 bytes per copy)
+  // with 16-byte stores; entry 63 (the correction) is written once the row's norm is
+  // known. The FP64 norm sums each group's FP32 squares.
   double acc = 0.0;
   for (int g0 = 0; g0 < groups; g0 += 32) {
     const int g = g0 + lane;
-    const int ng = min(32, groups - g0);  // groups of this pass
+    if (g >= groups) break;
     uint32_t hv[32], lv[32];  // 64 BF16 entries per copy, in pairs
     float part = 0.f;
 #pragma unroll
@@ -212,21 +202,13 @@ __global__ void __launch_bounds__(256)
       hv[pp] = *reinterpret_cast<const uint32_t*>(&hp);
       lv[pp] = *reinterpret_cast<const uint32_t*>(&lp);
     }
-    if (g < groups) acc += (double)part;
-    // hi, then lo: 16-byte chunk c of the pass is chunk c % 8 of group g0 + c / 8
+    acc += (double)part;
+    uint4* hd = reinterpret_cast<uint4*>(h2 + (size_t)g * 32);
+    uint4* ld = reinterpret_cast<uint4*>(l2 + (size_t)g * 32);
 #pragma unroll
-    for (int copy = 0; copy < 2; ++copy) {
-      const uint32_t* v = copy == 0 ? hv : lv;
-      if (g < groups) {
-        uint4* st4 = reinterpret_cast<uint4*>(sh + lane * 36);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) st4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
-      __syncwarp();
-      uint4* dst = reinterpret_cast<uint4*>((copy == 0 ? h2 : l2) + (size_t)g0 * 32);
-      for (int c = lane; c < ng * 8; c += 32)
-        dst[c] = *reinterpret_cast<const uint4*>(sh + (c >> 3) * 36 + (c & 7) * 4);
-      __syncwarp();
+    for (int v = 0; v < 8; ++v) {
+      hd[v] = make_uint4(hv[4 * v], hv[4 * v + 1], hv[4 * v + 2], hv[4 * v + 3]);
+      ld[v] = make_uint4(lv[4 * v], lv[4 * v + 1], lv[4 * v + 2], lv[4 * v + 3]);
     }
   }
 #pragma unroll
@@ -469,29 +451,25 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     }
     if (w.sym) {
       // column lists (not sorted): kColBatch records per lane are requested at once;
-      // the first 16 bytes of a record hold its count and first entry, the next 16
-      // bytes (same 32-byte sector) two more
-      constexpr int kColBatch = 8;
+      // the first 16 bytes of a record hold its count and first entry
+      constexpr int kColBatch = 4;
       for (int sb = s2_lo + lane; sb < s2_hi; sb += 32 * kColBatch) {
-        int4 h0[kColBatch], h1[kColBatch];
-        const int4* rp[kColBatch];
+        int4 h0[kColBatch];
+        long long ri[kColBatch];
 #pragma unroll
         for (int u = 0; u < kColBatch; ++u) {
           const int s2 = sb + 32 * u;
-          rp[u] = s2 < s2_hi && tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)
-                      ? reinterpret_cast<const int4*>(w.col_rec + collist(s2) * cp)
-                      : nullptr;
-          h0[u] = rp[u] ? __ldg(rp[u]) : make_int4(0, 0, 0, 0);
-          h1[u] = rp[u] ? __ldg(rp[u] + 1) : make_int4(0, 0, 0, 0);
+          ri[u] = s2 < s2_hi && tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)
+                      ? collist(s2) * cp : -1;
+          h0[u] = ri[u] >= 0 ? __ldg(reinterpret_cast<const int4*>(w.col_rec + ri[u]))
+                             : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < kColBatch; ++u) {
           const int nn = tk_in(h0[u].x, ks + 1, err) ? h0[u].x : 0;  // count <= k
           if (nn > 0 && __int_as_float(h0[u].w) <= thr) push(__int_as_float(h0[u].w), h0[u].z);
-          if (nn > 1 && __int_as_float(h1[u].y) <= thr) push(__int_as_float(h1[u].y), h1[u].x);
-          if (nn > 2 && __int_as_float(h1[u].w) <= thr) push(__int_as_float(h1[u].w), h1[u].z);
-          for (int p = 3; p < nn; ++p) {
-            const int2 e = __ldg(reinterpret_cast<const int2*>(rp[u]) + 1 + p);
+          for (int p = 1; p < nn; ++p) {
+            const int2 e = __ldg(reinterpret_cast<const int2*>(w.col_rec + ri[u]) + 1 + p);
             if (__int_as_float(e.y) <= thr) push(__int_as_float(e.y), e.x);
           }
         }

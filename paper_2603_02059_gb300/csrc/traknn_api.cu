@@ -47,6 +47,10 @@ struct TcPlan {
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
+// Host-buffer calls: the strips from this fraction of the series on run while the days
+// before them are copied in (the later strips hold less work: at the 75-year workload,
+// copy and compute of the two phases then overlap best).
+constexpr double kPhaseFrac = 0.55;
 
 struct GraphEntry {
   std::vector<int64_t> key;  // plan key, pointers and options
@@ -98,6 +102,9 @@ struct traknn_ctx {
   std::vector<std::pair<std::vector<int64_t>, int>> tuned;  // shape key -> tiles per unit
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
+  // host-buffer calls: copy stream and its events (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_io_free = nullptr, ev_late_in = nullptr, ev_early_in = nullptr;
 };
 
 namespace {
@@ -452,6 +459,94 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
 }
 
 
+// The launch sequence of a host-buffer call in two phases (plan built with a phase
+// strip, one series): the days the centring mean samples and the days [h0, N) are
+// copied in first (event late_in on the copy stream), the other days [0, h0) after
+// them (early_in). Strips from phase_strip on read only days >= h0 = phase_strip * R
+// (upper triangle: columns j >= T0 of the strip), so their band and main units run
+// as soon as those days are in, while the copy of the earlier days continues; then the
+// earlier days are prepared and the remaining strips run; one merge follows. The
+// operands, and so every distance, are those of the one-phase sequence; only the
+// order of the work units differs.
+traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cudaStream_t s,
+                                cudaEvent_t late_in, cudaEvent_t early_in) {
+  const TcPlan& p = h->plan;
+  const SeriesTable& sr = p.table;
+  const SeriesInfo& si = sr.s[0];
+  const int R = kTileRows - (si.L - 1);
+  const int h0 = p.phase_strip * R;
+  const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
+  const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
+  char* pd = static_cast<char*>(h->plan_dev);
+  TcArgs a;
+  a.Dp = b.Dp;
+  a.rows = p.rows;
+  a.out_rows = p.out_rows;
+  a.Lmax = p.Lmax;
+  a.kmax = p.kmax;
+  a.W = b.W;
+  a.part_d = b.part_d;
+  a.part_i = b.part_i;
+  a.err = h->err;
+  a.wait_limit_ns = (long long)h->wait_limit_ms * 1000000LL;
+  a.debug_withhold = h->debug_withhold;
+  a.seg_k = h->seg_k;
+  a.scratch = b.scratch;
+  a.groups = b.Dp / 64;
+  a.cval = b.cval;
+  a.l2_keep_a = h->l2_keep_a;
+  TcWork w;
+  w.units = reinterpret_cast<const WorkUnit*>(pd);
+  w.kstride = list_pitch(p.kmax);
+  w.col_off = reinterpret_cast<const long long*>(pd + ub);
+  w.slot_lo = reinterpret_cast<const int*>(pd + ub + cb);
+  w.sym = h->sym;
+  w.col_rec = b.col_rec;
+  w.col_ints = p.col_lists * col_pitch(w.kstride);
+  w.part_ints = p.part_lists * w.kstride;
+  w.thr = b.thr;
+  w.write_lists = 1;
+  w.stats = h->stats ? h->stats_dev : nullptr;
+  w.part_lo = 0;
+  w.part_hi = INT_MAX;
+  const bool split = h->precision == TRAKNN_PREC_SPLIT_BF16;
+  auto fused = [&](int u0, int nu, int ctr, bool band) -> cudaError_t {
+    if (nu <= 0) return cudaSuccess;
+    TcWork x = w;
+    x.units = w.units + u0;
+    x.nunits = nu;
+    x.counter = b.counter + ctr;
+    if (band) {
+      x.sym = 0;
+      x.write_lists = 0;
+    }
+    ++h->launches;
+    return launch_fused_tc(b.hi, b.lo, split, a, x, sr, h->sm_count, s);
+  };
+  // phase 1: the later days
+  TRY_CUDA(cudaStreamWaitEvent(s, late_in, 0));
+  TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
+  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, 1, b.Dp / 64, split, b.mu, h->weights,
+                                    b.hi, b.lo, b.norms, b.cval, s, h0));
+  TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s, h0));
+  TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
+  TRY_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
+  TRY_CUDA(fused(p.nunits, p.nband_a, 1, true));
+  TRY_CUDA(fused(0, p.nunits_a, 0, false));
+  // phase 2: the earlier days
+  TRY_CUDA(cudaStreamWaitEvent(s, early_in, 0));
+  TRY_CUDA(launch_prep_split_series(sr, h0, (int)D, 1, b.Dp / 64, split, b.mu, h->weights, b.hi,
+                                    b.lo, b.norms, b.cval, s, 0));
+  TRY_CUDA(launch_window_series(sr, std::min(h0, p.out_rows), b.norms, b.W, s, 0));
+  TRY_CUDA(fused(p.nunits + p.nband_a, p.nband - p.nband_a, 3, true));
+  TRY_CUDA(fused(p.nunits_a, p.nunits - p.nunits_a, 2, false));
+  w.nunits = p.nunits;
+  w.counter = b.counter;
+  TRY_CUDA(launch_merge_tc(a, w, sr, s));
+  h->launches += (h->center ? 2 : 1) + 4 + 1;
+  return TRAKNN_OK;
+}
+
 // Trajectory-embedded operands for a single-series tensor-core call: automatic for
 // small grids, where the fixed per-chunk cost of the epilogue (staging, window sums)
 // and not the contraction decides the time, so L times the Gram work costs little.
@@ -639,6 +734,9 @@ traknn_status traknn_destroy(traknn_handle h) {
   cudaDeviceSynchronize();
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  for (cudaEvent_t ev : {h->ev_io_free, h->ev_late_in, h->ev_early_in})
+    if (ev) cudaEventDestroy(ev);
   if (h->ws) cudaFree(h->ws);
   if (h->tcws) cudaFree(h->tcws);
   if (h->io) cudaFree(h->io);
@@ -911,8 +1009,56 @@ traknn_status traknn_knn_scores_host(traknn_handle h, const float* Xh, int64_t N
   int32_t* idx_d = reinterpret_cast<int32_t*>(io + xb);
   float* dist_d = reinterpret_cast<float*>(io + xb + ib);
   float* score_d = reinterpret_cast<float*>(io + xb + ib + db);
-  TRY_CUDA(cudaMemcpyAsync(Xd, Xh, (size_t)N * D * sizeof(float), cudaMemcpyHostToDevice, s));
-  TRY_ST(traknn_knn_scores(h, Xd, N, D, L, k, e, idx_d, dist_d, score_d, stream));
+  // Two phases when the series has enough strips: the copy of the later days, then of
+  // the earlier ones, on the copy stream; the strips of the later days start as soon
+  // as their days are in (see enqueue_tc_phased)
+  const int R = kTileRows - (L - 1);
+  const int strips = (int)((M + R - 1) / R);
+  const int phase_strip = (int)(kPhaseFrac * strips + 0.5);
+  const bool phased = h->precision != TRAKNN_PREC_FP32 && h->sym && !use_embedding(h, D, L) &&
+                      (!h->weights || h->weights_D == D) && strips >= 8 && tc_available();
+  if (!phased) {
+    TRY_CUDA(cudaMemcpyAsync(Xd, Xh, (size_t)N * D * sizeof(float), cudaMemcpyHostToDevice, s));
+    TRY_ST(traknn_knn_scores(h, Xd, N, D, L, k, e, idx_d, dist_d, score_d, stream));
+  } else {
+    if (!h->copy_stream) {
+      TRY_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+      TRY_CUDA(cudaEventCreateWithFlags(&h->ev_io_free, cudaEventDisableTiming));
+      TRY_CUDA(cudaEventCreateWithFlags(&h->ev_late_in, cudaEventDisableTiming));
+      TRY_CUDA(cudaEventCreateWithFlags(&h->ev_early_in, cudaEventDisableTiming));
+    }
+    const HostSeries sd{Xd, N, L, k, e, idx_d, dist_d, score_d};
+    TcBuffers buf;
+    TRY_ST(prepare_tc(h, &sd, 1, D, 8, false, 1, s, &buf, 0, INT_MAX, phase_strip));
+    const int64_t h0 = (int64_t)phase_strip * R;
+    const size_t row = (size_t)D * sizeof(float);
+    const int64_t ms = mean_stride((int)N);          // centring samples days 0, ms, 2ms, ...
+    const int64_t ns_e = (h0 + ms - 1) / ms;         // sampled days before h0
+    const cudaStream_t cs = h->copy_stream;
+    // the staging buffer is rewritten only after earlier work on `stream` is done
+    TRY_CUDA(cudaEventRecord(h->ev_io_free, s));
+    TRY_CUDA(cudaStreamWaitEvent(cs, h->ev_io_free, 0));
+    // 1. the sampled days before h0 (one strided copy), 2. the days [h0, N)
+    TRY_CUDA(cudaMemcpy2DAsync(Xd, ms * row, Xh, ms * row, row, (size_t)ns_e,
+                               cudaMemcpyHostToDevice, cs));
+    TRY_CUDA(cudaMemcpyAsync(Xd + h0 * D, Xh + h0 * D, (size_t)(N - h0) * row,
+                             cudaMemcpyHostToDevice, cs));
+    TRY_CUDA(cudaEventRecord(h->ev_late_in, cs));
+    // 3. the other days before h0: full gaps between sampled days (strided), then the
+    // last, shorter gap
+    if (ms > 1) {
+      const int64_t full = (h0 - 1) / ms;  // gaps [i ms + 1, (i+1) ms) inside [0, h0)
+      if (full > 0)
+        TRY_CUDA(cudaMemcpy2DAsync(Xd + D, ms * row, Xh + D, ms * row, (ms - 1) * row,
+                                   (size_t)full, cudaMemcpyHostToDevice, cs));
+      const int64_t r0 = full * ms + 1;
+      if (r0 < h0)
+        TRY_CUDA(cudaMemcpyAsync(Xd + r0 * D, Xh + r0 * D, (size_t)(h0 - r0) * row,
+                                 cudaMemcpyHostToDevice, cs));
+    }
+    TRY_CUDA(cudaEventRecord(h->ev_early_in, cs));
+    TRY_ST(enqueue_tc_phased(h, buf, D, s, h->ev_late_in, h->ev_early_in));
+  }
   TRY_CUDA(cudaMemcpyAsync(idx_h, idx_d, (size_t)M * k * sizeof(int32_t),
                            cudaMemcpyDeviceToHost, s));
   TRY_CUDA(cudaMemcpyAsync(dist_h, dist_d, (size_t)M * k * sizeof(float),

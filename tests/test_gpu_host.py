@@ -54,3 +54,32 @@ def test_host_entry_rejects_bad_shapes_without_work(tk):
         tk.knn_scores_host(X, 3, 9, 2, handle=h)  # 8 trajectories cannot have 9 neighbours
     assert ei.value.status == 2
     assert h.launch_count() == n0
+
+
+def test_host_entry_equals_device_entry_75y(tk):
+    """The 75-year workload through host buffers takes the two-phase sequence (the
+    later days' strips run while the earlier days are copied in): its results equal
+    the device entry point's bit for bit."""
+    import torch
+    X, meta, cfg = config_inputs("euro_75y_46x81")
+    L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
+    hidx, hdist, hscore = tk.knn_scores_host(torch.from_numpy(X).pin_memory(), L, k, e)
+    didx, ddist, dscore = tk.knn_scores(torch.from_numpy(X).cuda(), L, k, e)
+    torch.cuda.synchronize()
+    assert np.array_equal(hidx.numpy(), didx.cpu().numpy())
+    assert np.array_equal(hdist.numpy(), ddist.cpu().numpy())
+    assert np.array_equal(hscore.numpy(), dscore.cpu().numpy())
+
+
+def test_host_entry_with_grid_weights(tk):
+    import torch
+    X, _ = make_slp_like(2500, 12, 20, seed=63)
+    w = torch.linspace(0.2, 1.0, 240, device="cuda")
+    h = tk.Handle()
+    h.set_grid_weights(w)
+    hres = tk.knn_scores_host(torch.from_numpy(X).pin_memory(), 5, 10, 4, handle=h)
+    dres = tk.knn_scores(torch.from_numpy(X).cuda(), 5, 10, 4, handle=h)
+    torch.cuda.synchronize()
+    for a, b in zip(hres, dres):
+        assert np.array_equal(a.numpy(), b.cpu().numpy())
+    h.close()
