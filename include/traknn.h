@@ -97,12 +97,17 @@ typedef enum {
   TRAKNN_OPT_L2_KEEP_A = 12,         /* tensor-core paths: 1 loads a unit's row-strip operand with
                                         an L2 evict-last policy (it is re-read for every tile of
                                         the unit; default 0) */
-  TRAKNN_OPT_EMBED = 13              /* tensor-core traknn_knn_scores with L > 1: 1 builds one
+  TRAKNN_OPT_EMBED = 13,             /* tensor-core traknn_knn_scores with L > 1: 1 builds one
                                         operand row per trajectory (its L days, Eq. 1, L*D values)
                                         so that one Gram entry is the whole window sum of Eq. 2
                                         (L times the contraction, no diagonal sums); 2 never;
                                         0 (default) when L*D <= 1024, the small-grid form (Sec. 5:
                                         fields reduced to a few dozen principal components) */
+  TRAKNN_OPT_EPI_GROUPS = 14         /* tensor-core paths: 1 keeps one epilogue warpgroup; 0
+                                        (default) uses two at L = 1 (embedded operands included)
+                                        when the grid fits one accumulation segment and k <= 32,
+                                        each reading half of every tile's columns (the results
+                                        are the same) */
 } traknn_option;
 
 #define TRAKNN_MAX_L 17  /* longest trajectory (days) supported */

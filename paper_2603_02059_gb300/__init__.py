@@ -27,7 +27,7 @@ EMBED = {"auto": 0, "always": 1, "never": 2}
 OPTION = {"precision": 0, "center": 1, "col_chunks": 2, "wait_limit_ms": 3,
           "debug_withhold": 4, "profile": 5, "symmetric": 6, "unit_cols": 7, "stats": 8,
           "autotune": 9, "segment_k": 10,
-          "group_strips": 11, "l2_keep_a": 12, "embed": 13}
+          "group_strips": 11, "l2_keep_a": 12, "embed": 13, "epi_groups": 14}
 
 
 class Series(ctypes.Structure):

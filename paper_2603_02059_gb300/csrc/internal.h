@@ -233,6 +233,7 @@ struct TcArgs {
   const float* cval;   // [rows] correction value c of every stacked operand row
   int l2_keep_a;       // 1: load the strip operand with an L2 evict-last policy
   float* scratch;      // [CTAs][2][128 x 256] running tile totals (more than one segment)
+  int egroups;         // epilogue groups of the tensor-core kernel (1, or 2 at L = 1)
 };
 
 // Bytes of TcArgs::scratch for a launch of `num_ctas` CTAs.
@@ -336,6 +337,6 @@ size_t fused_fp32_smem_bytes(int k);
 // False until the tensor-core kernel is compiled in.
 bool tc_available();
 
-size_t fused_tc_smem_bytes(bool split, int kmax, int Lmax);
+size_t fused_tc_smem_bytes(bool split, int kmax, int Lmax, int G);
 
 }  // namespace traknn

@@ -54,8 +54,11 @@ constexpr int BM = kTileRows;  // accumulator rows (TMEM lanes)
 constexpr int BN = kTileCols;  // accumulator columns per tile (256)
 constexpr int KC = 32;         // K elements per stage (64 B rows, 64-B swizzle)
 constexpr int kEpiThreads = 128;  // one epilogue group: one thread per accumulator row
-// Threads of a CTA: warp 0 producer, warp 1 MMA issuer, four epilogue warps.
-constexpr int kThreads = 64 + kEpiThreads;
+// Threads of a CTA: warp 0 producer, warp 1 MMA issuer, G epilogue groups of four
+// warps. With G = 2 (L = 1 only: no window, no carry) group g reads the columns
+// [g 128, (g+1) 128) of every tile, so that twice as many warps hide the epilogue's
+// latencies when it, not the contraction, sets the pace (small grids).
+__host__ __device__ constexpr int kThreadsG(int G) { return 64 + kEpiThreads * G; }
 // Pitch of the Gram chunk buffer: 32 columns plus the L-1 carried ones, made odd
 // so that the diagonal reads of 32 consecutive rows hit 32 different banks.
 __host__ __device__ constexpr int chunk_pitch(int L) {
@@ -219,8 +222,8 @@ __device__ __forceinline__ float kth_of(const RegList<K>& l, int k) {
 
 constexpr int kQueue = 4;  // depth of the per-CTA unit queue
 
-template <int K>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int K, int G>
+__global__ void __launch_bounds__(kThreadsG(G), 1)
     fused_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                     const __grid_constant__ CUtensorMap tmA_lo,
                     const __grid_constant__ CUtensorMap tmB_hi,
@@ -237,16 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t ring = (raw + 1023u) & ~1023u;
   unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
-  // epilogue region, sized for the largest L and k of the call
+  // epilogue regions (one per group), sized for the largest L and k of the call
   const size_t gbytes = group_bytes(a.kmax, a.Lmax);
-  float* Gbuf = reinterpret_cast<float*>(gptr);
-  float* Wsh = Gbuf + BM * chunk_pitch(a.Lmax);  // window sums of the tile's output columns
-  float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
-  float* Csh = Tsh + BN;         // correction values c of the tile's Gram columns
-  uint32_t* Cmask = reinterpret_cast<uint32_t*>(Csh + BN);  // [4][32] column-side row masks
-  float* Cld = reinterpret_cast<float*>(Cmask + 128);  // [kmax][32] column-side lists
-  int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * a.kmax);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + gbytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + G * gbytes);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = full0 + 8u * NS;
   const uint32_t tfull0 = empty0 + 8u * NS;
@@ -270,12 +266,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(tfull0 + 8u * b, 1);
-      ptx::mbar_init(tempty0 + 8u * b, kEpiThreads);
+      ptx::mbar_init(tempty0 + 8u * b, kEpiThreads * G);  // every epilogue thread
     }
     ptx::mbar_init(drain, 1);
     for (int i = 0; i < kQueue; ++i) {
       ptx::mbar_init(qfull0 + 8u * i, 1);
-      ptx::mbar_init(qempty0 + 8u * i, 2);  // the MMA thread and the epilogue leader
+      ptx::mbar_init(qempty0 + 8u * i, 1 + G);  // the MMA thread and each group's leader
     }
 
     *abort_flag = 0;
@@ -456,11 +452,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
+    const int gid = (warp - 2) >> 2;  // epilogue group
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
     const int l = q * 32 + lane;     // accumulator row owned by this thread
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-    const int et = threadIdx.x - 64;  // 0..127 within the epilogue
-    const int bar = 1;                // the epilogue's named barrier
+    const int et = threadIdx.x - 64 - kEpiThreads * gid;  // 0..127 within the group
+    const int bar = 1 + gid;          // the group's named barrier
+    // the group's chunks of every tile
+    const int ch_lo = gid * (BN / 32 / G), ch_hi = ch_lo + BN / 32 / G;
+    // the group's shared memory
+    float* Gbuf = reinterpret_cast<float*>(gptr + gid * gbytes);
+    float* Wsh = Gbuf + BM * chunk_pitch(a.Lmax);  // window sums of the tile's output columns
+    float* Tsh = Wsh + BN;         // row bounds of the tile's output columns (column side)
+    float* Csh = Tsh + BN;         // correction values c of the tile's Gram columns
+    uint32_t* Cmask = reinterpret_cast<uint32_t*>(Csh + BN);  // [4][32] column-side row masks
+    float* Cld = reinterpret_cast<float*>(Cmask + 128);  // [kmax][32] column-side lists
+    int32_t* Cli = reinterpret_cast<int32_t*>(Cld + 32 * a.kmax);
     const long long cpitch = col_pitch(w.kstride);  // ints per column-list record
     const int cx = ((warp - 2) & 3) * 8 + (lane & 7);      // column-side column of lanes 0..7
     int qs = 0, gch = 0, gt = 0;
@@ -468,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     UnitSpan us;
     // phase timing of the first epilogue thread (diagnostics)
-    const bool timed = w.stats != nullptr && et == 0;
+    const bool timed = w.stats != nullptr && et == 0 && gid == 0;
     long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
     // event counts kept per thread, summed once at the end (diagnostics)
     unsigned int cnt[5] = {0, 0, 0, 0, 0};
@@ -586,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool released = false;
         for (int sj = 0; sj < nser; ++sj) {
         if (nser > 1 && !unit_span(w, p.sr.s, u, sj, us)) continue;
-        const int L = us.L;
+        const int L = G == 2 ? 1 : us.L;  // two groups run only at L = 1
         const int LDG = chunk_pitch(L);
         const int t = us.T0 + l;
         const bool row_ok = l < us.R && t < us.M;
@@ -622,12 +629,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t vr[32];
         if (kAhead) {
           if (nseg == 1)
-            ptx::tmem_ld32_async(tlast, vr);
+            ptx::tmem_ld32_async(tlast + (uint32_t)(ch_lo * 32), vr);
           else
-            load_scr(gt, 0, vr);
+            load_scr(gt, ch_lo, vr);
         }
 #pragma unroll 1
-        for (int ch = 0; ch < BN / 32; ++ch) {
+        for (int ch = ch_lo; ch < ch_hi; ++ch) {
           if (!kAhead) {
             if (nseg == 1)
               ptx::tmem_ld32_async(tlast + (uint32_t)(ch * 32), vr);
@@ -659,13 +666,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int x = 0; x < 32; ++x) grow[(L - 1) + x] = c[x];
           }
-          if (kAhead && ch + 1 < BN / 32) {
+          if (kAhead && ch + 1 < ch_hi) {
             if (nseg == 1)
               ptx::tmem_ld32_async(tlast + (uint32_t)((ch + 1) * 32), vr);
             else
               load_scr(gt, ch + 1, vr);
           }
-          if (ch == BN / 32 - 1 && sj == nser - 1) {
+          if (ch == ch_hi - 1 && sj == nser - 1) {
             // the accumulator has been read out: hand it back to the MMA warp
             ptx::tc_fence_before();
             ptx::mbar_arrive(tempty0 + 8u * acc_l);
@@ -836,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (row_ok && w.write_lists && (nser > 1 || it == ntiles - 1)) {
           const size_t base =
-              (size_t)(us.part_base + (long long)t * us.slots + us.slot) * w.kstride;
+              (size_t)(us.part_base + (long long)t * us.slots + us.slot * G + gid) * w.kstride;
 #pragma unroll
           for (int pp = 0; pp < K; ++pp) {
             if (pp < us.k) {
@@ -912,25 +919,25 @@ bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t epilogue_bytes(int k, int L) {
-  return group_bytes(k, L) + 8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
+size_t epilogue_bytes(int k, int L, int G) {
+  return G * group_bytes(k, L) + 8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
 }
 
-int pick_stages(bool split, int k, int L) {
+int pick_stages(bool split, int k, int L, int G) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k, L);
+  const size_t avail = kSmemLimit - 1024 - epilogue_bytes(k, L, G);
   int ns = (int)(avail / stage);
   return ns < kMaxStages ? ns : kMaxStages;
 }
 
-template <int K>
+template <int K, int G>
 cudaError_t launch_k(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUtensorMap& mBh,
                      const CUtensorMap& mBl, const TcParams& p, int num_ctas, size_t smem,
                      cudaStream_t st) {
-  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K>,
+  cudaError_t err = cudaFuncSetAttribute(fused_tc_kernel<K, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  fused_tc_kernel<K><<<num_ctas, kThreads, smem, st>>>(mAh, mAl, mBh, mBl, p);
+  fused_tc_kernel<K, G><<<num_ctas, kThreadsG(G), smem, st>>>(mAh, mAl, mBh, mBl, p);
   return cudaGetLastError();
 }
 
@@ -938,9 +945,10 @@ cudaError_t launch_k(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUten
 
 bool tc_available() { return encode_fn() != nullptr; }
 
-size_t fused_tc_smem_bytes(bool split, int kmax, int Lmax) {
+size_t fused_tc_smem_bytes(bool split, int kmax, int Lmax, int G) {
   const uint32_t stage = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  return 1024 + (size_t)pick_stages(split, kmax, Lmax) * stage + epilogue_bytes(kmax, Lmax);
+  return 1024 + (size_t)pick_stages(split, kmax, Lmax, G) * stage +
+         epilogue_bytes(kmax, Lmax, G);
 }
 
 cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const TcArgs& a,
@@ -962,21 +970,34 @@ cudaError_t launch_fused_tc(const void* hi, const void* lo, bool split, const Tc
   p.sr = sr;
   p.split = split ? 1 : 0;
   p.stage_bytes = split ? 2 * kTileA + 2 * kTileB : kTileA + kTileB;
-  p.nstages = pick_stages(split, a.kmax, a.Lmax);
+  const int G = a.egroups;
+  // two epilogue groups: L = 1, one accumulation segment, k <= 32 (host-checked here
+  // too: the kernel's two-group form has no window, carry or segment folding)
+  if (G != 1 && (G != 2 || a.Lmax != 1 || a.kmax > 32 || a.Dp > a.seg_k))
+    return cudaErrorInvalidValue;
+  p.nstages = pick_stages(split, a.kmax, a.Lmax, G);
   if (p.nstages < 2) return cudaErrorInvalidValue;
   if (a.seg_k < KC || a.seg_k % KC != 0) return cudaErrorInvalidValue;
   p.seg_kb = a.seg_k / KC;
-  const size_t smem = fused_tc_smem_bytes(split, a.kmax, a.Lmax);
+  const size_t smem = fused_tc_smem_bytes(split, a.kmax, a.Lmax, G);
   const int k = a.kmax;
-  if (k <= 4) return launch_k<4>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 8) return launch_k<8>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 10) return launch_k<10>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 16) return launch_k<16>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 20) return launch_k<20>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 32) return launch_k<32>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 40) return launch_k<40>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  if (k <= 48) return launch_k<48>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
-  return launch_k<64>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (G == 2) {
+    if (k <= 4) return launch_k<4, 2>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+    if (k <= 8) return launch_k<8, 2>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+    if (k <= 10) return launch_k<10, 2>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+    if (k <= 16) return launch_k<16, 2>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+    if (k <= 20) return launch_k<20, 2>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+    return launch_k<32, 2>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  }
+  if (k <= 4) return launch_k<4, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 8) return launch_k<8, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 10) return launch_k<10, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 16) return launch_k<16, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 20) return launch_k<20, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 32) return launch_k<32, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 40) return launch_k<40, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  if (k <= 48) return launch_k<48, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
+  return launch_k<64, 1>(mAh, mAl, mBh, mBl, p, num_ctas, smem, st);
 }
 
 }  // namespace traknn

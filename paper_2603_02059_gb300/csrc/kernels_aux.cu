@@ -139,7 +139,7 @@ __global__ void col_final_series_kernel(const __grid_constant__ SeriesTable st,
 // row-major input are the contiguous values X + a*D .. X + (a+emb)*D. The Gram of
 // such rows is the diagonal window sum of Eq. 2 (sum over m of <x_{a+m}, x_{b+m}>),
 // and the norm of a row is the window sum of the day norms.
-template <bool kCorr>
+template <bool kCorr, bool kEmb>
 __global__ void __launch_bounds__(256)
     prep_split_series_kernel(const __grid_constant__ SeriesTable st, int r_lo, int rows, int D,
                              int emb, int groups, const float* __restrict__ mu,
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256)
   const int Dlen = emb * D;  // values of one operand row
   // grid-point weights w_p enter the distance as sqrt(w_p) scalings of the values
   auto val = [&](int i) {
-    const int pnt = emb > 1 ? i % D : i;  // grid point of value i
+    const int pnt = kEmb ? i % D : i;  // grid point of value i
     return wts ? (x[i] - m[pnt]) * sqrtf(wts[pnt]) : x[i] - m[pnt];
   };
   // One read of the row. Lane g0 + lane builds group g0 + lane: its entry pos is grid
@@ -451,24 +451,27 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     }
     if (w.sym) {
       // column lists (not sorted): kColBatch records per lane are requested at once;
-      // the first 16 bytes of a record hold its count and first entry
+      // the first 32 bytes of a record (one sector) hold its count and three entries
       constexpr int kColBatch = 4;
       for (int sb = s2_lo + lane; sb < s2_hi; sb += 32 * kColBatch) {
-        int4 h0[kColBatch];
+        int4 h0[kColBatch], h1[kColBatch];
         long long ri[kColBatch];
 #pragma unroll
         for (int u = 0; u < kColBatch; ++u) {
           const int s2 = sb + 32 * u;
           ri[u] = s2 < s2_hi && tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)
                       ? collist(s2) * cp : -1;
-          h0[u] = ri[u] >= 0 ? __ldg(reinterpret_cast<const int4*>(w.col_rec + ri[u]))
-                             : make_int4(0, 0, 0, 0);
+          const int4* r4 = reinterpret_cast<const int4*>(w.col_rec + (ri[u] >= 0 ? ri[u] : 0));
+          h0[u] = ri[u] >= 0 ? __ldg(r4) : make_int4(0, 0, 0, 0);
+          h1[u] = ri[u] >= 0 ? __ldg(r4 + 1) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < kColBatch; ++u) {
           const int nn = tk_in(h0[u].x, ks + 1, err) ? h0[u].x : 0;  // count <= k
           if (nn > 0 && __int_as_float(h0[u].w) <= thr) push(__int_as_float(h0[u].w), h0[u].z);
-          for (int p = 1; p < nn; ++p) {
+          if (nn > 1 && __int_as_float(h1[u].y) <= thr) push(__int_as_float(h1[u].y), h1[u].x);
+          if (nn > 2 && __int_as_float(h1[u].w) <= thr) push(__int_as_float(h1[u].w), h1[u].z);
+          for (int p = 3; p < nn; ++p) {
             const int2 e = __ldg(reinterpret_cast<const int2*>(w.col_rec + ri[u]) + 1 + p);
             if (__int_as_float(e.y) <= thr) push(__int_as_float(e.y), e.x);
           }
@@ -579,14 +582,23 @@ cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int
                                      int r_lo) {
   if (rows <= r_lo) return cudaSuccess;
   const int blocks = (rows - r_lo + 7) / 8;
-  if (correct)
-    prep_split_series_kernel<true><<<blocks, 256, 0, st>>>(
-        sr, r_lo, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
-        static_cast<__nv_bfloat16*>(lo), norms, cval);
+  __nv_bfloat16* h = static_cast<__nv_bfloat16*>(hi);
+  __nv_bfloat16* l = static_cast<__nv_bfloat16*>(lo);
+  // the embedded form (values of several days per row) maps a value to its grid point
+  // by a division; the plain form needs none
+  if (correct && emb > 1)
+    prep_split_series_kernel<true, true><<<blocks, 256, 0, st>>>(sr, r_lo, rows, D, emb, groups,
+                                                                 mu, wts, h, l, norms, cval);
+  else if (correct)
+    prep_split_series_kernel<true, false><<<blocks, 256, 0, st>>>(sr, r_lo, rows, D, emb, groups,
+                                                                  mu, wts, h, l, norms, cval);
+  else if (emb > 1)
+    prep_split_series_kernel<false, true><<<blocks, 256, 0, st>>>(sr, r_lo, rows, D, emb, groups,
+                                                                  mu, wts, h, l, norms, cval);
   else
-    prep_split_series_kernel<false><<<blocks, 256, 0, st>>>(
-        sr, r_lo, rows, D, emb, groups, mu, wts, static_cast<__nv_bfloat16*>(hi),
-        static_cast<__nv_bfloat16*>(lo), norms, cval);
+    prep_split_series_kernel<false, false><<<blocks, 256, 0, st>>>(sr, r_lo, rows, D, emb,
+                                                                   groups, mu, wts, h, l, norms,
+                                                                   cval);
   return cudaGetLastError();
 }
 

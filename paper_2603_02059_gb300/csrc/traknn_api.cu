@@ -44,6 +44,7 @@ struct TcPlan {
   // main units, then band units, are the first nunits_a / nband_a of each list), so
   // they can run while the days before phase_strip are still being copied in.
   int phase_strip = 0, nunits_a = 0, nband_a = 0;
+  int egroups = 1;  // epilogue groups of the fused kernel; each writes its own row lists
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
@@ -92,6 +93,7 @@ struct traknn_ctx {
   int group_strips = 0;
   int l2_keep_a = 0;
   int embed = 0;  // 0: automatic, 1: always, 2: never (TRAKNN_OPT_EMBED)
+  int epi_groups = 0;  // 0: automatic, 1: one epilogue group (TRAKNN_OPT_EPI_GROUPS)
   const float* weights = nullptr;  // [weights_D] grid-point weights (caller-owned), or null
   int64_t weights_D = 0;
   int stats = 0;
@@ -170,7 +172,7 @@ inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
 // (smallest L, most trajectories) defines the units' column ranges.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
                 int group_opt, bool shared, int part_lo, int part_hi, int phase_strip,
-                TcPlan& p) {
+                int egroups, TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
@@ -190,7 +192,8 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     const int step = kTileCols - (Lg - 1);
     const int strips = (M + R - 1) / R;
     const int cols = shared ? step : cols_opt > 0 ? cols_opt : tiles * kTileCols - (Lg - 1);
-    const int slots = (M + cols - 1) / cols;
+    // row-side list slots per trajectory row: one per column range and epilogue group
+    const int slots = (M + cols - 1) / cols * egroups;
     SeriesInfo& si = p.table.s[b];
     si.N = N;
     si.M = M;
@@ -210,7 +213,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
       p.col_off.push_back(off);
       const long long first_col = (long long)(s + 1) * R;
       if (sym && first_col < M) off += M - first_col;
-      p.slot_lo.push_back(sym ? (s * R) / cols : 0);
+      p.slot_lo.push_back(sym ? (s * R) / cols * egroups : 0);
     }
     const int nser = shared ? B : 1;
     if (!shared || b == 0) {
@@ -252,6 +255,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     p.Lmax = std::max(p.Lmax, L);
   }
   p.phase_strip = phase_strip;
+  p.egroups = egroups;
   p.nunits_a = (int)p.units.size();
   p.nband_a = (int)band.size();
   p.units.insert(p.units.end(), later.begin(), later.end());
@@ -346,10 +350,22 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   key.push_back(part_lo);
   key.push_back(part_hi);
   key.push_back(phase_strip);
+  // two epilogue groups for L = 1 (small grids through embedded operands) when the
+  // tile has one accumulation segment and the lists are short
+  int Lmax = 1, kmax = 1;
+  for (int b = 0; b < B; ++b) {
+    Lmax = std::max(Lmax, sd[b].L);
+    kmax = std::max(kmax, sd[b].k);
+  }
+  const int egroups = (h->epi_groups != 1 && !shared && Lmax == 1 && kmax <= 32 &&
+                       tc_groups((int)D * emb) * 64 <= h->seg_k)
+                          ? 2
+                          : 1;
+  key.push_back(egroups);
   TcPlan& p = h->plan;
   if (p.key != key) {
     build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, part_lo, part_hi,
-               phase_strip, p);
+               phase_strip, egroups, p);
     p.key = key;
     p.emb = emb;
     p.part_lo = part_lo;
@@ -408,6 +424,7 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   a.groups = b.Dp / 64;
   a.cval = b.cval;
   a.l2_keep_a = h->l2_keep_a;
+  a.egroups = p.egroups;
 
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
@@ -495,6 +512,7 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
   a.groups = b.Dp / 64;
   a.cval = b.cval;
   a.l2_keep_a = h->l2_keep_a;
+  a.egroups = p.egroups;
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
   w.kstride = list_pitch(p.kmax);
@@ -789,6 +807,10 @@ traknn_status traknn_set_option(traknn_handle h, traknn_option opt, int64_t v) {
     case TRAKNN_OPT_EMBED:
       if (v < 0 || v > 2) return TRAKNN_ERR_INVALID_ARG;
       h->embed = (int)v;
+      return TRAKNN_OK;
+    case TRAKNN_OPT_EPI_GROUPS:
+      if (v < 0 || v > 1) return TRAKNN_ERR_INVALID_ARG;
+      h->epi_groups = (int)v;
       return TRAKNN_OK;
     case TRAKNN_OPT_GROUP_STRIPS:
       if (v < 0 || v > 4096) return TRAKNN_ERR_INVALID_ARG;

@@ -81,6 +81,8 @@ CASES = [  # N, h, w, L, k, e, options
     (1500, 8, 12, 5, 10, 4, dict(precision="split_bf16", symmetric=0, embed=2)),
     (900, 40, 60, 5, 10, 4, dict(precision="split_bf16", segment_k=256)),
     (777, 9, 15, 10, 20, 9, dict(precision="bf16", embed=2)),
+    (1500, 4, 8, 5, 20, 4, dict(precision="split_bf16", embed=1)),  # two epilogue groups
+    (600, 3, 4, 1, 8, 0, dict(precision="split_bf16")),  # two epilogue groups, L = 1
 ]
 
 

@@ -90,3 +90,25 @@ def test_embedded_and_window_forms_agree(tk, small_d_75y):
     rel = np.abs(a[1] - b[1]) / np.maximum(b[1], 1e-30)
     assert rel.max() <= 2 * TOL
     assert np.allclose(a[2], b[2], rtol=2 * TOL)
+
+
+@pytest.mark.parametrize("N,h,w,L,k,e,embed", [(2000, 4, 8, 5, 20, 4, "always"),
+                                               (1500, 3, 5, 1, 10, 0, "never"),
+                                               (900, 2, 4, 10, 32, 9, "always"),
+                                               (700, 6, 6, 3, 4, 2, "always")])
+def test_two_epilogue_groups_equal_one(tk, N, h, w, L, k, e, embed):
+    """At L = 1 (embedded operands included) two epilogue groups split every tile's
+    columns; the neighbour lists, distances and scores are those of one group."""
+    import torch
+    X, _ = make_slp_like(N, h, w, seed=7 * N + L)
+    Xd = torch.from_numpy(X).cuda()
+    hd = tk.Handle()
+    two = [t.cpu().numpy() for t in tk.knn_scores(Xd, L, k, e, embed=embed, handle=hd)]
+    hd.set_option("epi_groups", 1)
+    one = [t.cpu().numpy() for t in tk.knn_scores(Xd, L, k, e, embed=embed, handle=hd)]
+    torch.cuda.synchronize()
+    assert hd.sync_status() == 0
+    for a, b in zip(one, two):
+        assert np.array_equal(a, b)
+    check_full(X, L, k, e, *two, TOL)
+    hd.close()
