@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int gid = (warp - 2) >> 2;  // epilogue group
+    const int gid = G == 1 ? 0 : (warp - 2) >> 2;  // epilogue group
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
     const int l = q * 32 + lane;     // accumulator row owned by this thread
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;

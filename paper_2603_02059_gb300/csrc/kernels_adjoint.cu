@@ -91,10 +91,12 @@ __device__ void sift_down(int* a, int root, int n) {
   }
 }
 
-constexpr int kAdjR = 32;         // output days per block
+constexpr int kAdjR = 16;         // output days per block
 constexpr int kKeyCap = 4096;     // incidences sorted at once in shared memory
 constexpr int kBuildThreads = 256;
-constexpr int kGatherCols = 256;  // grid points per gather CTA (one per thread)
+constexpr int kGatherThreads = 256;
+constexpr int kGatherV = 2;       // grid points per gather thread (kGatherThreads apart)
+constexpr int kGatherCols = kGatherThreads * kGatherV;  // grid points per gather CTA
 
 // One merged entry of a block's gradient list: partner day b and summed weight w
 // (as FP32 bits). A block's entries are in order of output day (blk_day gives each
@@ -333,17 +335,17 @@ __global__ void __launch_bounds__(kBuildThreads)
 
 // dX for one block of kAdjR days and kGatherCols grid points: for each day a0 + d,
 // every entry (b, w) of the day adds w (X[a0+d] - X[b]), in list order. Each thread
-// owns one grid point and keeps the block's kAdjR values of X and sums in registers.
-// The entries (the same for every thread) are staged in shared memory kStage at a
-// time, and partner values are loaded kU at a time so that kU loads per thread (and
-// about 64 KB per SM) are in flight: the kernel is bound by the latency of these L2
-// reads. blockIdx.x is the day block and blockIdx.y the grid-point tile: CTAs are
-// scheduled with x fastest, so the CTAs running at one time share a tile of X, which
-// stays in L2 while the entries re-read its rows (consecutive days of a block share
-// many partner rows, which then also come from L1).
-constexpr int kU = 32;
+// owns kGatherV grid points (kGatherThreads apart, so every warp load is coalesced)
+// and keeps the block's values of X and sums for them in registers; one entry (read
+// from shared memory, the same for every thread) serves all of them. Partner values
+// are loaded kU entries at a time (kU * kGatherV loads per thread in flight). blockIdx.x
+// is the day block and blockIdx.y the grid-point tile: CTAs are scheduled with x
+// fastest, so the CTAs running at one time share a tile of X, which stays in L2 while
+// the entries re-read its rows (consecutive days of a block share many partner rows,
+// which then also come from L1).
+constexpr int kU = 16;
 constexpr int kStage = 2048;
-__global__ void __launch_bounds__(kGatherCols, 2)
+__global__ void __launch_bounds__(kGatherThreads, 2)
     adj_gather_kernel(const float* __restrict__ X, int N, int D,
                       const long long* __restrict__ blk_off, const int* __restrict__ blk_day,
                       const AdjEntry* __restrict__ ent, const float* __restrict__ wts,
@@ -359,19 +361,26 @@ __global__ void __launch_bounds__(kGatherCols, 2)
   const int ntot = sday[kAdjR];
   const int tiles = (D + kGatherCols - 1) / kGatherCols;
   for (int tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
-    const int p = tile * kGatherCols + tid;
-    const bool pin = p < D;
-    const float* xp = X + (pin ? p : 0);
-    float xa[kAdjR], acc[kAdjR];
+    const int p0 = tile * kGatherCols + tid;
+    bool pin[kGatherV];
+    const float* xp[kGatherV];
 #pragma unroll
-    for (int d = 0; d < kAdjR; ++d) {
-      xa[d] = (pin && d < nd) ? __ldg(xp + (size_t)(a0 + d) * D) : 0.f;
-      acc[d] = 0.f;
+    for (int v = 0; v < kGatherV; ++v) {
+      pin[v] = p0 + v * kGatherThreads < D;
+      xp[v] = X + (pin[v] ? p0 + v * kGatherThreads : 0);
     }
+    float xa[kAdjR][kGatherV], acc[kAdjR][kGatherV];
+#pragma unroll
+    for (int d = 0; d < kAdjR; ++d)
+#pragma unroll
+      for (int v = 0; v < kGatherV; ++v) {
+        xa[d][v] = (pin[v] && d < nd) ? __ldg(xp[v] + (size_t)(a0 + d) * D) : 0.f;
+        acc[d][v] = 0.f;
+      }
     for (int c0 = 0; c0 < ntot; c0 += kStage) {
       const int c1 = min(ntot, c0 + kStage);
       __syncthreads();  // the previous pass has read its entries
-      for (int i = tid; i < c1 - c0; i += kGatherCols) {
+      for (int i = tid; i < c1 - c0; i += kGatherThreads) {
         AdjEntry e = __ldg(e2 + c0 + i);
         if (!tk_in(e.x, N, err)) e = make_int2(a0, 0);  // debug build: adds 0
         se[i] = e;
@@ -380,22 +389,51 @@ __global__ void __launch_bounds__(kGatherCols, 2)
 #pragma unroll
       for (int d = 0; d < kAdjR; ++d) {
         const int q1 = min(sday[d + 1], c1);
-        for (int q = max(sday[d], c0); q < q1; q += kU) {
-          float xb[kU];
+        int q = max(sday[d], c0);
+        // whole groups of kU entries, then the remainder with predicated loads
+        for (; q + kU <= q1; q += kU) {
+          float xb[kU][kGatherV];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const size_t off = (size_t)se[q + u - c0].x * D;
+#pragma unroll
+            for (int v = 0; v < kGatherV; ++v) xb[u][v] = pin[v] ? __ldg(xp[v] + off) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const float w = __int_as_float(se[q + u - c0].y);
+#pragma unroll
+            for (int v = 0; v < kGatherV; ++v) acc[d][v] = fmaf(w, xa[d][v] - xb[u][v], acc[d][v]);
+          }
+        }
+        if (q < q1) {
+          float xb[kU][kGatherV];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const size_t off = q + u < q1 ? (size_t)se[q + u - c0].x * D : 0;
+#pragma unroll
+            for (int v = 0; v < kGatherV; ++v)
+              xb[u][v] = (pin[v] && q + u < q1) ? __ldg(xp[v] + off) : 0.f;
+          }
 #pragma unroll
           for (int u = 0; u < kU; ++u)
-            xb[u] = (pin && q + u < q1) ? __ldg(xp + (size_t)se[q + u - c0].x * D) : 0.f;
+            if (q + u < q1) {
+              const float w = __int_as_float(se[q + u - c0].y);
 #pragma unroll
-          for (int u = 0; u < kU; ++u)
-            if (q + u < q1) acc[d] = fmaf(__int_as_float(se[q + u - c0].y), xa[d] - xb[u], acc[d]);
+              for (int v = 0; v < kGatherV; ++v)
+                acc[d][v] = fmaf(w, xa[d][v] - xb[u][v], acc[d][v]);
+            }
         }
       }
     }
-    if (pin) {
+#pragma unroll
+    for (int v = 0; v < kGatherV; ++v) {
+      if (!pin[v]) continue;
+      const int p = p0 + v * kGatherThreads;
       const float wp = wts ? wts[p] : 1.f;
 #pragma unroll
       for (int d = 0; d < kAdjR; ++d)
-        if (d < nd) dX[(size_t)(a0 + d) * D + p] = wts ? acc[d] * wp : acc[d];
+        if (d < nd) dX[(size_t)(a0 + d) * D + p] = wts ? acc[d][v] * wp : acc[d][v];
     }
   }
 }
@@ -455,7 +493,8 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
                                                     blk_day, ent, err);
   const int tiles = (D + kGatherCols - 1) / kGatherCols;
   const dim3 grid(nblk, tiles < 65535 ? tiles : 65535);
-  adj_gather_kernel<<<grid, kGatherCols, 0, st>>>(X, N, D, blk_off, blk_day, ent, wts, dX, err);
+  adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(X, N, D, blk_off, blk_day, ent, wts, dX,
+                                                      err);
   *launches += 7;
   return cudaGetLastError();
 }

@@ -450,9 +450,9 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
     }
     if (w.sym) {
-      // column lists (not sorted): kColBatch records per lane are requested at once;
-      // the first 32 bytes of a record (one sector) hold its count and three entries
-      constexpr int kColBatch = 4;
+      // column lists (not sorted): the first 32 bytes of a record (one sector, two
+      // loads in flight together) hold its count and three entries
+      constexpr int kColBatch = 1;
       for (int sb = s2_lo + lane; sb < s2_hi; sb += 32 * kColBatch) {
         int4 h0[kColBatch], h1[kColBatch];
         long long ri[kColBatch];
