@@ -338,12 +338,16 @@ def run_e2e(tk, h, X, L, k, e, prec, steps, ws, device):
     for _ in range(2):
         tk.knn_scores_host(Xh, L, k, e, precision=prec, handle=h, out=outh)
     barrier(ws)
-    t0 = time.perf_counter()
     n = max(1, steps)
+    calls = []
+    t0 = time.perf_counter()
     for _ in range(n):
+        t1 = time.perf_counter()
         tk.knn_scores_host(Xh, L, k, e, precision=prec, handle=h, out=outh)
+        calls.append((time.perf_counter() - t1) * 1e3)
     ms = reduce_max((time.perf_counter() - t0) * 1e3 / n, ws, device)
     return {"value": aggregate(pairs, ms, ws), "unit": "pairs/s", "ms_per_step": ms,
+            "ms_per_call_median": statistics.median(calls), "ms_per_call_min": min(calls),
             "h2d_bytes_per_step": X.nbytes,
             "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outh),
             "api": "traknn_knn_scores_host (pinned host buffers)"}

@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
   const uint32_t tmem_base = *tmem_slot;
   const int nkb = a.Dp / KC;
   const int seg_kb = p.seg_kb;                    // K blocks per accumulation segment
-  const int nseg = (nkb + seg_kb - 1) / seg_kb;   // segments per tile
+  // segments per tile (the two-group form runs with one segment: checked on the host)
+  const int nseg = G == 2 ? 1 : (nkb + seg_kb - 1) / seg_kb;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -475,7 +476,8 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
     bool ok = true;
     UnitSpan us;
     // phase timing of the first epilogue thread (diagnostics)
-    const bool timed = w.stats != nullptr && et == 0 && gid == 0;
+    // (the two-group form keeps no phase timers: its registers are scarcer)
+    const bool timed = G == 1 && w.stats != nullptr && et == 0 && gid == 0;
     long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
     // event counts kept per thread, summed once at the end (diagnostics)
     unsigned int cnt[5] = {0, 0, 0, 0, 0};
@@ -623,9 +625,11 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
         // segment, else the scratch partial total (the last segment's chunk is
         // added from TMEM when the chunk is staged)
         const uint32_t tlast = tmem_base + lane_addr + (uint32_t)(acc_l * BN);
-        // with the largest lists the chunk is fetched when it is staged instead (the
-        // prefetched registers would otherwise stay live across the scan and spill)
-        constexpr bool kAhead = K <= 40;
+        // with the largest lists, and with two epilogue groups (168 registers a thread;
+        // the other group hides the latency), the chunk is fetched when it is staged
+        // instead (the prefetched registers would otherwise stay live across the scan
+        // and spill)
+        constexpr bool kAhead = K <= 40 && G == 1;
         uint32_t vr[32];
         if (kAhead) {
           if (nseg == 1)
