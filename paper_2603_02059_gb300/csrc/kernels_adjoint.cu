@@ -95,8 +95,6 @@ constexpr int kAdjR = 16;         // output days per block
 constexpr int kKeyCap = 4096;     // incidences sorted at once in shared memory
 constexpr int kBuildThreads = 256;
 constexpr int kGatherThreads = 256;
-constexpr int kGatherV = 2;       // grid points per gather thread (kGatherThreads apart)
-constexpr int kGatherCols = kGatherThreads * kGatherV;  // grid points per gather CTA
 
 // One merged entry of a block's gradient list: partner day b and summed weight w
 // (as FP32 bits). A block's entries are in order of output day (blk_day gives each
@@ -333,23 +331,52 @@ __global__ void __launch_bounds__(kBuildThreads)
   }
 }
 
-// dX for one block of kAdjR days and kGatherCols grid points: for each day a0 + d,
-// every entry (b, w) of the day adds w (X[a0+d] - X[b]), in list order. Each thread
-// owns kGatherV grid points (kGatherThreads apart, so every warp load is coalesced)
-// and keeps the block's values of X and sums for them in registers; one entry (read
-// from shared memory, the same for every thread) serves all of them. Partner values
-// are loaded kU entries at a time (kU * kGatherV loads per thread in flight). blockIdx.x
-// is the day block and blockIdx.y the grid-point tile: CTAs are scheduled with x
-// fastest, so the CTAs running at one time share a tile of X, which stays in L2 while
-// the entries re-read its rows (consecutive days of a block share many partner rows,
-// which then also come from L1).
+// Values of V adjacent grid points (V = 2: one 8-byte load; rows are 8-byte aligned
+// when D is even) and the update acc += w (xa - xb) on them, with V = 2 as two packed
+// FP32 operations (xa - xb exactly as xb * -1 + xa, then one fused multiply-add).
+template <int V> struct Vec;
+template <> struct Vec<1> {
+  typedef float T;
+  static __device__ __forceinline__ T load(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ T zero() { return 0.f; }
+  static __device__ __forceinline__ void update(T& acc, float w, T xa, T xb) {
+    acc = fmaf(w, xa - xb, acc);
+  }
+  static __device__ __forceinline__ float get(T v, int) { return v; }
+};
+template <> struct Vec<2> {
+  typedef float2 T;
+  static __device__ __forceinline__ T load(const float* p) {
+    return __ldg(reinterpret_cast<const float2*>(p));
+  }
+  static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void update(T& acc, float w, T xa, T xb) {
+    const float2 d = __ffma2_rn(xb, make_float2(-1.f, -1.f), xa);
+    acc = __ffma2_rn(make_float2(w, w), d, acc);
+  }
+  static __device__ __forceinline__ float get(T v, int i) { return i ? v.y : v.x; }
+};
+
+// dX for one block of kAdjR days and kGatherThreads * V grid points: for each day
+// a0 + d, every entry (b, w) of the day adds w (X[a0+d] - X[b]), in list order. Each
+// thread owns V adjacent grid points and keeps the block's values of X and sums for
+// them in registers; one entry (read from shared memory, the same for every thread)
+// serves all of them. Partner values are loaded kU entries at a time (kU loads per
+// thread in flight). blockIdx.x is the day block and blockIdx.y the grid-point tile:
+// CTAs are scheduled with x fastest, so the CTAs running at one time share a tile of
+// X, which stays in L2 while the entries re-read its rows (consecutive days of a
+// block share many partner rows, which then also come from L1).
 constexpr int kU = 16;
 constexpr int kStage = 2048;
+template <int V>
 __global__ void __launch_bounds__(kGatherThreads, 2)
     adj_gather_kernel(const float* __restrict__ X, int N, int D,
                       const long long* __restrict__ blk_off, const int* __restrict__ blk_day,
                       const AdjEntry* __restrict__ ent, const float* __restrict__ wts,
                       float* __restrict__ dX, int* err) {
+  typedef Vec<V> Op;
+  typedef typename Op::T T;
+  constexpr int kCols = kGatherThreads * V;
   __shared__ AdjEntry se[kStage];
   __shared__ int sday[kAdjR + 1];
   const int tid = threadIdx.x;
@@ -359,24 +386,17 @@ __global__ void __launch_bounds__(kGatherThreads, 2)
   if (tid <= kAdjR) sday[tid] = blk_day[blockIdx.x * (kAdjR + 1) + tid];
   __syncthreads();
   const int ntot = sday[kAdjR];
-  const int tiles = (D + kGatherCols - 1) / kGatherCols;
+  const int tiles = (D + kCols - 1) / kCols;
   for (int tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
-    const int p0 = tile * kGatherCols + tid;
-    bool pin[kGatherV];
-    const float* xp[kGatherV];
+    const int p = tile * kCols + V * tid;  // first of the thread's V grid points
+    const bool pin = p < D;                // (D is a multiple of V)
+    const float* xp = X + (pin ? p : 0);
+    T xa[kAdjR], acc[kAdjR];
 #pragma unroll
-    for (int v = 0; v < kGatherV; ++v) {
-      pin[v] = p0 + v * kGatherThreads < D;
-      xp[v] = X + (pin[v] ? p0 + v * kGatherThreads : 0);
+    for (int d = 0; d < kAdjR; ++d) {
+      xa[d] = (pin && d < nd) ? Op::load(xp + (size_t)(a0 + d) * D) : Op::zero();
+      acc[d] = Op::zero();
     }
-    float xa[kAdjR][kGatherV], acc[kAdjR][kGatherV];
-#pragma unroll
-    for (int d = 0; d < kAdjR; ++d)
-#pragma unroll
-      for (int v = 0; v < kGatherV; ++v) {
-        xa[d][v] = (pin[v] && d < nd) ? __ldg(xp[v] + (size_t)(a0 + d) * D) : 0.f;
-        acc[d][v] = 0.f;
-      }
     for (int c0 = 0; c0 < ntot; c0 += kStage) {
       const int c1 = min(ntot, c0 + kStage);
       __syncthreads();  // the previous pass has read its entries
@@ -392,48 +412,35 @@ __global__ void __launch_bounds__(kGatherThreads, 2)
         int q = max(sday[d], c0);
         // whole groups of kU entries, then the remainder with predicated loads
         for (; q + kU <= q1; q += kU) {
-          float xb[kU][kGatherV];
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const size_t off = (size_t)se[q + u - c0].x * D;
-#pragma unroll
-            for (int v = 0; v < kGatherV; ++v) xb[u][v] = pin[v] ? __ldg(xp[v] + off) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const float w = __int_as_float(se[q + u - c0].y);
-#pragma unroll
-            for (int v = 0; v < kGatherV; ++v) acc[d][v] = fmaf(w, xa[d][v] - xb[u][v], acc[d][v]);
-          }
-        }
-        if (q < q1) {
-          float xb[kU][kGatherV];
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const size_t off = q + u < q1 ? (size_t)se[q + u - c0].x * D : 0;
-#pragma unroll
-            for (int v = 0; v < kGatherV; ++v)
-              xb[u][v] = (pin[v] && q + u < q1) ? __ldg(xp[v] + off) : 0.f;
-          }
+          T xb[kU];
 #pragma unroll
           for (int u = 0; u < kU; ++u)
-            if (q + u < q1) {
-              const float w = __int_as_float(se[q + u - c0].y);
+            xb[u] = pin ? Op::load(xp + (size_t)se[q + u - c0].x * D) : Op::zero();
 #pragma unroll
-              for (int v = 0; v < kGatherV; ++v)
-                acc[d][v] = fmaf(w, xa[d][v] - xb[u][v], acc[d][v]);
-            }
+          for (int u = 0; u < kU; ++u)
+            Op::update(acc[d], __int_as_float(se[q + u - c0].y), xa[d], xb[u]);
+        }
+        if (q < q1) {
+          T xb[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u)
+            xb[u] = (pin && q + u < q1) ? Op::load(xp + (size_t)se[q + u - c0].x * D)
+                                        : Op::zero();
+#pragma unroll
+          for (int u = 0; u < kU; ++u)
+            if (q + u < q1) Op::update(acc[d], __int_as_float(se[q + u - c0].y), xa[d], xb[u]);
         }
       }
     }
+    if (pin) {
 #pragma unroll
-    for (int v = 0; v < kGatherV; ++v) {
-      if (!pin[v]) continue;
-      const int p = p0 + v * kGatherThreads;
-      const float wp = wts ? wts[p] : 1.f;
+      for (int v = 0; v < V; ++v) {
+        const float wp = wts ? wts[p + v] : 1.f;
 #pragma unroll
-      for (int d = 0; d < kAdjR; ++d)
-        if (d < nd) dX[(size_t)(a0 + d) * D + p] = wts ? acc[d][v] * wp : acc[d][v];
+        for (int d = 0; d < kAdjR; ++d)
+          if (d < nd) dX[(size_t)(a0 + d) * D + p + v] = wts ? Op::get(acc[d], v) * wp
+                                                             : Op::get(acc[d], v);
+      }
     }
   }
 }
@@ -491,10 +498,16 @@ cudaError_t launch_adjoint(const float* X, int N, int D, int L, int k, const int
   adj_block_scan_kernel<<<1, 1024, 0, st>>>(off, N, L, M, k, nblk, blk_off);
   adj_build_kernel<<<nblk, kBuildThreads, 0, st>>>(idx, g, N, L, M, k, off, rev, blk_off,
                                                     blk_day, ent, err);
-  const int tiles = (D + kGatherCols - 1) / kGatherCols;
+  // two adjacent grid points per thread when rows are 8-byte aligned (D even)
+  const int V = D % 2 == 0 ? 2 : 1;
+  const int tiles = (D + kGatherThreads * V - 1) / (kGatherThreads * V);
   const dim3 grid(nblk, tiles < 65535 ? tiles : 65535);
-  adj_gather_kernel<<<grid, kGatherThreads, 0, st>>>(X, N, D, blk_off, blk_day, ent, wts, dX,
-                                                      err);
+  if (V == 2)
+    adj_gather_kernel<2><<<grid, kGatherThreads, 0, st>>>(X, N, D, blk_off, blk_day, ent, wts,
+                                                          dX, err);
+  else
+    adj_gather_kernel<1><<<grid, kGatherThreads, 0, st>>>(X, N, D, blk_off, blk_day, ent, wts,
+                                                          dX, err);
   *launches += 7;
   return cudaGetLastError();
 }

@@ -146,9 +146,12 @@ __global__ void __launch_bounds__(256)
                              const float* __restrict__ wts, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
                              float* __restrict__ cval) {
+  // per warp: 32 finished groups of one copy (36-word rows: 16-byte aligned)
+  __shared__ __align__(16) uint32_t stage[8][32 * 36];
   const int r = r_lo + blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
+  uint32_t* sh = stage[threadIdx.x >> 5];
   const int b = find_series(st.s, st.n, r, false);
   const SeriesInfo& si = st.s[b];
   const int a = r - si.row_base;
@@ -177,13 +180,14 @@ __global__ void __launch_bounds__(256)
   };
   // One read of the row. Lane g0 + lane builds group g0 + lane: its entry pos is grid
   // point pos * groups + g, so for each pos the warp reads 32 consecutive grid points
-  // (coalesced), and each lane writes its group's 64 entries (128 bytes per copy)
-  // with 16-byte stores; entry 63 (the correction) is written once the row's norm is
-  // known. The FP64 norm sums each group's FP32 squares.
+  // (coalesced). The warp's 32 groups, contiguous in the output row, are staged in
+  // shared memory (one copy at a time) and written with contiguous 16-byte stores;
+  // entry 63 (the correction) is written once the row's norm is known. The FP64 norm
+  // sums each group's FP32 squares.
   double acc = 0.0;
   for (int g0 = 0; g0 < groups; g0 += 32) {
     const int g = g0 + lane;
-    if (g >= groups) break;
+    const int ng = min(32, groups - g0);  // groups of this pass
     uint32_t hv[32], lv[32];  // 64 BF16 entries per copy, in pairs
     float part = 0.f;
 #pragma unroll
@@ -202,13 +206,22 @@ __global__ void __launch_bounds__(256)
       hv[pp] = *reinterpret_cast<const uint32_t*>(&hp);
       lv[pp] = *reinterpret_cast<const uint32_t*>(&lp);
     }
-    acc += (double)part;
-    uint4* hd = reinterpret_cast<uint4*>(h2 + (size_t)g * 32);
-    uint4* ld = reinterpret_cast<uint4*>(l2 + (size_t)g * 32);
+    if (g < groups) acc += (double)part;
+    // hi, then lo: 16-byte chunk c of the pass is chunk c % 8 of group g0 + c / 8
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      hd[v] = make_uint4(hv[4 * v], hv[4 * v + 1], hv[4 * v + 2], hv[4 * v + 3]);
-      ld[v] = make_uint4(lv[4 * v], lv[4 * v + 1], lv[4 * v + 2], lv[4 * v + 3]);
+    for (int copy = 0; copy < 2; ++copy) {
+      const uint32_t* v = copy == 0 ? hv : lv;
+      if (g < groups) {
+        uint4* st4 = reinterpret_cast<uint4*>(sh + lane * 36);
+#pragma unroll
+        for (int q4 = 0; q4 < 8; ++q4)
+          st4[q4] = make_uint4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+      }
+      __syncwarp();
+      uint4* dst = reinterpret_cast<uint4*>((copy == 0 ? h2 : l2) + (size_t)g0 * 32);
+      for (int c = lane; c < ng * 8; c += 32)
+        dst[c] = *reinterpret_cast<const uint4*>(sh + (c >> 3) * 36 + (c & 7) * 4);
+      __syncwarp();
     }
   }
 #pragma unroll
