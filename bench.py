@@ -492,14 +492,20 @@ def suite_batched(args):
 
     ms_seq = _events_ms(seq, args.steps, 3)
     ms_bat = _events_ms(bat, args.steps, 3)
+    tiles, group = h.work_shape()
+    # the same batched call with the default work-unit shape (8 tiles, 19 strips)
     h.set_option("autotune", 0)
+    ms_def = _events_ms(lambda: tk.knn_scores_batched(series, handle=h, outs=outs),
+                        args.steps, 3)
     if h.sync_status() != 0:
         raise RuntimeError("device-side failure")
     return {"suite": "batched", "series": len(shapes), "D": 46 * 81,
             "total_days": sum(s[0] for s in shapes), "pairs_per_step": pairs,
             "batched": {"ms_per_step": ms_bat, "pairs_per_s": pairs / (ms_bat * 1e-3)},
             "sequential": {"ms_per_step": ms_seq, "pairs_per_s": pairs / (ms_seq * 1e-3)},
-            "speedup": ms_seq / ms_bat}
+            "speedup": ms_seq / ms_bat,
+            "autotuned_shape": {"tiles_per_unit": tiles, "group_strips": group},
+            "default_shape_ms_per_step": ms_def, "autotune_speedup": ms_def / ms_bat}
 
 
 def suite_adjoint(args):

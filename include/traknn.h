@@ -84,9 +84,12 @@ typedef enum {
                                         (upper triangle, Sec. 3.3), 0 both triangles (default 1) */
   TRAKNN_OPT_UNIT_COLS = 7,          /* tensor-core paths: output columns per work unit, 0 = auto */
   TRAKNN_OPT_STATS = 8,              /* 1: count kernel events (read with traknn_stats_read) */
-  TRAKNN_OPT_AUTOTUNE = 9,           /* tensor-core paths: 1 times 4, 8 and 16 Gram tiles per work
-                                        unit on the first call of each shape and keeps the fastest
-                                        (ignored while TRAKNN_OPT_UNIT_COLS is set; default 0) */
+  TRAKNN_OPT_AUTOTUNE = 9,           /* tensor-core paths: 1 times every work-unit shape of
+                                        {4, 8, 16} Gram tiles per unit x {10, 19, 38} row strips
+                                        run side by side (the strips only while
+                                        TRAKNN_OPT_GROUP_STRIPS is 0) on the first call of each
+                                        problem shape and keeps the fastest (ignored while
+                                        TRAKNN_OPT_UNIT_COLS is set; default 0) */
   TRAKNN_OPT_SEGMENT_K = 10,         /* tensor-core paths: the tensor cores accumulate at most this
                                         many grid points (a multiple of 32) of a Gram entry before
                                         the partial sum is added in FP32 to the entry's running
@@ -328,6 +331,11 @@ traknn_status traknn_profile_read(traknn_handle handle, float* ms, int max_n, in
  * scan up to the barrier after it, [13] in the column side, [14] in total (all
  * summed over CTAs). Synchronises the device and resets them. */
 traknn_status traknn_stats_read(traknn_handle handle, uint64_t* counters, int n);
+
+/* Work-unit shape of the handle's last tensor-core forward call (the autotuner's
+ * choice when TRAKNN_OPT_AUTOTUNE is on): Gram tiles per work unit and row strips
+ * whose units run side by side. Both 0 before the first such call. */
+traknn_status traknn_work_shape(traknn_handle handle, int* tiles_per_unit, int* group_strips);
 
 /* Total number of kernels this handle has launched (all entry points). */
 traknn_status traknn_launch_count(traknn_handle handle, int64_t* count);

@@ -84,6 +84,7 @@ def bind(path: str):
         "traknn_partition": [I64, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "traknn_knn_partial": [P, P, I64, I64, I, I, I, I, I, P, P, P],
         "traknn_merge_partials": [P, P, P, I, I64, I, P, P, P, P],
+        "traknn_work_shape": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -183,6 +184,13 @@ class Handle:
         buf = (ctypes.c_uint64 * len(names))()
         _check(lib().traknn_stats_read(self._h, buf, len(names)), "stats_read")
         return {n: int(buf[i]) for i, n in enumerate(names)}
+
+    def work_shape(self):
+        """(Gram tiles per work unit, row strips side by side) of the last tensor-core
+        forward call (the autotuner's choice when autotuning is on)."""
+        t, g = ctypes.c_int(), ctypes.c_int()
+        _check(lib().traknn_work_shape(self._h, ctypes.byref(t), ctypes.byref(g)), "work_shape")
+        return int(t.value), int(g.value)
 
     def launch_count(self) -> int:
         c = ctypes.c_int64()

@@ -101,7 +101,9 @@ struct traknn_ctx {
   TcPlan plan;
   void* plan_dev = nullptr;  // units, col_off, slot_lo of `plan`
   size_t plan_dev_bytes = 0;
-  std::vector<std::pair<std::vector<int64_t>, int>> tuned;  // shape key -> tiles per unit
+  // shape key -> (tiles per unit, strips side by side) chosen by the autotuner
+  std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tuned;
+  int last_tiles = 0, last_group = 0;  // work-unit shape of the last tensor-core call
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   // host-buffer calls: copy stream and its events (created on first use)
@@ -342,9 +344,12 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
 // and size the workspace. Must not run during a stream capture.
 traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
                          bool shared, int emb, cudaStream_t s, TcBuffers* out,
-                         int part_lo = 0, int part_hi = INT_MAX, int phase_strip = 0) {
+                         int part_lo = 0, int part_hi = INT_MAX, int phase_strip = 0,
+                         int group = 0) {
+  if (group <= 0) group = h->group_strips;  // 0: the planner's default
   std::vector<int64_t> key = shape_key(sd, B, D, h);
   key.push_back(tiles);
+  key.push_back(group);
   key.push_back(shared ? 1 : 0);
   key.push_back(emb);
   key.push_back(part_lo);
@@ -364,7 +369,7 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   key.push_back(egroups);
   TcPlan& p = h->plan;
   if (p.key != key) {
-    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, h->group_strips, shared, part_lo, part_hi,
+    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, group, shared, part_lo, part_hi,
                phase_strip, egroups, p);
     p.key = key;
     p.emb = emb;
@@ -588,43 +593,52 @@ traknn_status validate_series(const HostSeries* sd, int B, int64_t D) {
   return TRAKNN_OK;
 }
 
-// Tiles per work unit for this batch shape: the autotuned value when tuning is on
-// (each candidate timed once after a warm-up launch, the fastest kept per shape),
-// else 8.
-traknn_status pick_tiles(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
-                         int* tiles) {
+// Work-unit shape for this batch: Gram tiles per unit and row strips whose units run
+// side by side (sharing operand tiles in L2). With tuning on (and neither set by an
+// option) every pair of {4, 8, 16} tiles and {10, 19, 38} strips is timed once after a
+// warm-up launch and the fastest is kept per shape; else 8 tiles and the default
+// grouping (19 strips, or the option's value).
+traknn_status pick_shape(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
+                         int* tiles, int* group) {
   *tiles = 8;
+  *group = 0;
   if (!h->autotune || h->unit_cols > 0) return TRAKNN_OK;
   const std::vector<int64_t> key = shape_key(sd, B, D, h);
   for (auto& t : h->tuned)
     if (t.first == key) {
-      *tiles = t.second;
+      *tiles = t.second.first;
+      *group = t.second.second;
       return TRAKNN_OK;
     }
   cudaEvent_t e0, e1;
   TRY_CUDA(cudaEventCreate(&e0));
   TRY_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_t = 8;
-  for (int cand : {4, 8, 16}) {
-    TcBuffers buf;
-    TRY_ST(prepare_tc(h, sd, B, D, cand, false, 1, s, &buf));
-    TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
-    TRY_CUDA(cudaEventRecord(e0, s));
-    TRY_ST(enqueue_tc(h, buf, D, s, false));
-    TRY_CUDA(cudaEventRecord(e1, s));
-    TRY_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      best_t = cand;
+  int best_t = 8, best_g = 0;
+  const std::vector<int> groups = h->group_strips > 0 ? std::vector<int>{h->group_strips}
+                                                      : std::vector<int>{10, 19, 38};
+  for (int cand_g : groups)
+    for (int cand_t : {4, 8, 16}) {
+      TcBuffers buf;
+      TRY_ST(prepare_tc(h, sd, B, D, cand_t, false, 1, s, &buf, 0, INT_MAX, 0, cand_g));
+      TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
+      TRY_CUDA(cudaEventRecord(e0, s));
+      TRY_ST(enqueue_tc(h, buf, D, s, false));
+      TRY_CUDA(cudaEventRecord(e1, s));
+      TRY_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_t = cand_t;
+        best_g = cand_g;
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->tuned.emplace_back(key, best_t);
+  h->tuned.emplace_back(key, std::make_pair(best_t, best_g));
   *tiles = best_t;
+  *group = best_g;
   return TRAKNN_OK;
 }
 
@@ -634,11 +648,13 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
                      bool graph, bool shared = false, int emb = 1, int part_lo = 0,
                      int part_hi = INT_MAX) {
   if (!tc_available()) return TRAKNN_ERR_UNSUPPORTED;
-  int tiles = 8;
+  int tiles = 8, group = 0;
   const bool whole = part_lo == 0 && part_hi == INT_MAX;
-  if (!shared && emb == 1 && whole) TRY_ST(pick_tiles(h, sd, B, D, s, &tiles));
+  if (!shared && emb == 1 && whole) TRY_ST(pick_shape(h, sd, B, D, s, &tiles, &group));
   TcBuffers buf;
-  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi));
+  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi, 0, group));
+  h->last_tiles = tiles;
+  h->last_group = group > 0 ? group : (h->group_strips > 0 ? h->group_strips : 19);
   if (!graph) return enqueue_tc(h, buf, D, s, h->profile != 0);
 
   std::vector<int64_t> key = h->plan.key;
@@ -1148,6 +1164,13 @@ traknn_status traknn_stats_read(traknn_handle h, uint64_t* counters, int n) {
     TRY_CUDA(cudaMemset(h->stats_dev, 0, sizeof(buf)));
   }
   for (int i = 0; i < n && i < kStatCount; ++i) counters[i] = buf[i];
+  return TRAKNN_OK;
+}
+
+traknn_status traknn_work_shape(traknn_handle h, int* tiles_per_unit, int* group_strips) {
+  if (!h || !tiles_per_unit || !group_strips) return TRAKNN_ERR_INVALID_ARG;
+  *tiles_per_unit = h->last_tiles;
+  *group_strips = h->last_group;
   return TRAKNN_OK;
 }
 

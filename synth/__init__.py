@@ -166,6 +166,10 @@ CONFIGS = {
     # 75 years on the 0.25-degree grid (181x321 = 58,101 points).
     "euro_75y_181x321": dict(n_days=27394, h=181, w=321, L=5, k=20, exclusion=4,
                              gen=dict(annual_amp=5.0)),
+    # 75 years of 32-value fields (4x8 grid): a stand-in for fields reduced to a few
+    # dozen principal components (the small-grid form).
+    "small_d_75y_4x8": dict(n_days=27394, h=4, w=8, L=5, k=20, exclusion=4,
+                            gen=dict(annual_amp=5.0)),
 }
 
 SEED_BASE = 20260302
