@@ -91,7 +91,7 @@ __device__ void sift_down(int* a, int root, int n) {
   }
 }
 
-constexpr int kAdjR = 8;          // output days per block
+constexpr int kAdjR = 16;         // output days per block
 constexpr int kKeyCap = 4096;     // incidences sorted at once in shared memory
 constexpr int kBuildThreads = 256;
 constexpr int kGatherThreads = 256;
@@ -366,7 +366,7 @@ template <> struct Vec<2> {
 // CTAs are scheduled with x fastest, so the CTAs running at one time share a tile of
 // X, which stays in L2 while the entries re-read its rows (consecutive days of a
 // block share many partner rows, which then also come from L1).
-constexpr int kU = 32;
+constexpr int kU = 16;
 constexpr int kStage = 2048;
 template <int V>
 __global__ void __launch_bounds__(kGatherThreads, 2)
