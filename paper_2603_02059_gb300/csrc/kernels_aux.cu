@@ -240,6 +240,97 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same operand preparation for rows of few groups (groups <= 16, e.g. the
+// trajectory-embedded rows of a small grid): a warp takes 32 / groups rows at once,
+// lane (r, g) = (lane / groups, lane % groups) building group g of row r, so that no
+// lane idles; the row's FP64 norm is summed over its lanes in a fixed order. The grid
+// point of value i (i mod D) is stepped along with i instead of divided.
+template <bool kCorr>
+__global__ void __launch_bounds__(256)
+    prep_split_small_kernel(const __grid_constant__ SeriesTable st, int r_lo, int rows, int D,
+                            int emb, int groups, const float* __restrict__ mu,
+                            const float* __restrict__ wts, __nv_bfloat16* __restrict__ hi,
+                            __nv_bfloat16* __restrict__ lo, double* __restrict__ norms,
+                            float* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  const int per_warp = 32 / groups;
+  const int rl = lane / groups, g = lane - rl * groups;  // row of the warp, group of the row
+  const int r = r_lo + (blockIdx.x * 8 + (threadIdx.x >> 5)) * per_warp + rl;
+  const bool act = rl < per_warp && r < rows;
+  const int Dp = groups * 64;
+  double part = 0.0;
+  int b = 0;
+  bool pad = true;
+  if (act) {
+    b = find_series(st.s, st.n, r, false);
+    const SeriesInfo& si = st.s[b];
+    const int a = r - si.row_base;
+    pad = a >= si.N;
+    uint4* hd = reinterpret_cast<uint4*>(hi + (size_t)r * Dp + g * 64);
+    uint4* ld = reinterpret_cast<uint4*>(lo + (size_t)r * Dp + g * 64);
+    uint32_t hv[32], lv[32];
+    float fp = 0.f;
+    if (!pad) {
+      const float* x = si.X + (size_t)a * D;
+      const float* m = mu + (size_t)b * D;
+      const int Dlen = emb * D;
+      int pnt = g % D;  // grid point of value i = pos * groups + g, stepped with pos
+#pragma unroll
+      for (int pp = 0; pp < 32; ++pp) {
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pos = 2 * pp + h, i = pos * groups + g;
+          float val = 0.f;
+          if (i < Dlen && pos < 63) {
+            val = x[i] - m[pnt];
+            if (wts) val *= sqrtf(wts[pnt]);
+          }
+          v[h] = val;
+          pnt += groups;  // groups <= D (emb <= 17 < 63), so one subtraction suffices
+          if (pnt >= D) pnt -= D;
+        }
+        fp = fmaf(v[0], v[0], fp);
+        fp = fmaf(v[1], v[1], fp);
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]);
+        const __nv_bfloat16 q0 = __float2bfloat16_rn(v[0] - __bfloat162float(h0));
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[1]);
+        const __nv_bfloat16 q1 = __float2bfloat16_rn(v[1] - __bfloat162float(h1));
+        const __nv_bfloat162 hp = __halves2bfloat162(h0, h1);
+        const __nv_bfloat162 lp = __halves2bfloat162(q0, q1);
+        hv[pp] = *reinterpret_cast<const uint32_t*>(&hp);
+        lv[pp] = *reinterpret_cast<const uint32_t*>(&lp);
+      }
+    } else {
+#pragma unroll
+      for (int pp = 0; pp < 32; ++pp) hv[pp] = lv[pp] = 0u;
+    }
+    part = (double)fp;
+#pragma unroll
+    for (int q4 = 0; q4 < 8; ++q4) {
+      hd[q4] = make_uint4(hv[4 * q4], hv[4 * q4 + 1], hv[4 * q4 + 2], hv[4 * q4 + 3]);
+      ld[q4] = make_uint4(lv[4 * q4], lv[4 * q4 + 1], lv[4 * q4 + 2], lv[4 * q4 + 3]);
+    }
+  }
+  // the row's norm: its groups' FP32 sums added in group order by the row's first lane
+  double acc = 0.0;
+  const int first = rl * groups;
+  for (int j = 0; j < groups; ++j) {
+    const double pj = __shfl_sync(0xffffffffu, part, min(31, first + j));
+    acc += pj;
+  }
+  if (!act) return;
+  const float c = (kCorr && !pad)
+                      ? __bfloat162float(__float2bfloat16_rn((float)sqrt(acc / groups)))
+                      : 0.f;
+  hi[(size_t)r * Dp + g * 64 + 63] = __float2bfloat16_rn(c);
+  lo[(size_t)r * Dp + g * 64 + 63] = __float2bfloat16_rn(-c);
+  if (g == 0) {
+    norms[r] = pad ? 0.0 : acc;
+    cval[r] = c;
+  }
+}
+
 // W of every stacked trajectory row: an explicit L-term FP64 sum of its series' norms.
 __global__ void window_series_kernel(const __grid_constant__ SeriesTable st, int r_lo,
                                      int out_rows, const double* __restrict__ norms, float* W) {
@@ -380,6 +471,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
   __shared__ float bd[kMergeWarps][kMergeCap];
   __shared__ int bi[kMergeWarps][kMergeCap];
   __shared__ int bn[kMergeWarps];
+  __shared__ float sorted_d[kMergeWarps][kMaxK];  // the row's k distances in order
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * kMergeWarps + wid;
   if (r >= out_rows) return;
@@ -403,33 +495,101 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       bi[wid][pos] = i;
     }
   };
-  auto select = [&](int n) {
-    float last_d = -CUDART_INF_F;
-    int last_i = -1;
-    for (int rr = 0; rr < k; ++rr) {
-      float best_d = CUDART_INF_F;
-      int best_i = INT_MAX;
-      for (int q = lane; q < n; q += 32) {
-        const float d = bd[wid][q];
-        const int ii = bi[wid][q];
-        if (key_less(last_d, last_i, d, ii) && key_less(d, ii, best_d, best_i)) {
-          best_d = d;
-          best_i = ii;
-        }
-      }
+  // The k smallest (distance, index) keys among the n <= kMergeCap buffered
+  // candidates (distinct keys): a binary search on the distance bits (distances are
+  // >= 0, so their bit patterns order like the values) finds the k-th distance T;
+  // among candidates tied at T the smallest indices are taken (a second search on the
+  // index, only when there are more ties than places). Returns T; with `out` the k
+  // keys are written to the row's outputs in (distance, index) order (index -1,
+  // distance +inf for missing ones) with the FP64 mean of the k distances, summed in
+  // that order.
+  auto select_k = [&](int n, bool out) -> float {
+    constexpr int kPer = kMergeCap / 32;
+    unsigned db[kPer];
+    int ib[kPer];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float od = __shfl_xor_sync(0xffffffffu, best_d, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, best_i, o);
-        if (key_less(od, oi, best_d, best_i)) {
-          best_d = od;
-          best_i = oi;
-        }
-      }
-      last_d = best_d;
-      last_i = best_i;
+    for (int u = 0; u < kPer; ++u) {
+      const int q = lane + 32 * u;
+      db[u] = q < n ? (__float_as_uint(bd[wid][q]) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+      ib[u] = q < n ? bi[wid][q] : INT_MAX;
     }
-    return last_d;
+    auto count_le = [&](unsigned x) {
+      unsigned c = 0;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) c += db[u] <= x ? 1u : 0u;
+      return (int)__reduce_add_sync(0xffffffffu, c);
+    };
+    const unsigned kInf = 0x7F800000u;
+    const int kk = min(k, count_le(kInf));  // candidates with a distance (not NaN)
+    unsigned T = kInf;
+    int I = INT_MAX;
+    if (kk > 0) {
+      unsigned lo = 0, hi = kInf;
+      while (lo < hi) {
+        const unsigned mid = lo + ((hi - lo) >> 1);
+        if (count_le(mid) >= kk) hi = mid;
+        else lo = mid + 1;
+      }
+      T = lo;
+      const int less = T > 0 ? count_le(T - 1) : 0;
+      const int need = kk - less;  // places for candidates at distance T (>= 1)
+      unsigned ceq = 0;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) ceq += db[u] == T ? 1u : 0u;
+      if ((int)__reduce_add_sync(0xffffffffu, ceq) > need) {
+        int lo2 = 0, hi2 = INT_MAX;
+        while (lo2 < hi2) {
+          const int mid = lo2 + ((hi2 - lo2) >> 1);
+          unsigned c = 0;
+#pragma unroll
+          for (int u = 0; u < kPer; ++u) c += (db[u] == T && ib[u] <= mid) ? 1u : 0u;
+          if ((int)__reduce_add_sync(0xffffffffu, c) >= need) hi2 = mid;
+          else lo2 = mid + 1;
+        }
+        I = lo2;
+      }
+    }
+    if (!out) return __uint_as_float(T);
+    // compact the selected keys to the front of the buffer, then place each by rank
+    float dv[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) dv[u] = lane + 32 * u < n ? bd[wid][lane + 32 * u] : 0.f;
+    __syncwarp();
+    int base = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const bool sel = kk > 0 && (db[u] < T || (db[u] == T && ib[u] <= I));
+      const unsigned m = __ballot_sync(0xffffffffu, sel);
+      if (sel) {
+        const int q = base + __popc(m & ((1u << lane) - 1u));
+        bd[wid][q] = dv[u];
+        bi[wid][q] = ib[u];
+      }
+      base += __popc(m);
+    }
+    __syncwarp();
+    for (int e = lane; e < k; e += 32) {
+      if (e < kk) {
+        const float de = bd[wid][e];
+        const int ie = bi[wid][e];
+        int rank = 0;
+        for (int j = 0; j < kk; ++j) rank += key_less(bd[wid][j], bi[wid][j], de, ie) ? 1 : 0;
+        si.idx[(size_t)t * k + rank] = ie;
+        si.dist[(size_t)t * k + rank] = de;
+        sorted_d[wid][rank] = de;
+      } else {
+        si.idx[(size_t)t * k + e] = -1;
+        si.dist[(size_t)t * k + e] = CUDART_INF_F;
+        sorted_d[wid][e] = CUDART_INF_F;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      double sum = 0.0;
+      for (int e = 0; e < k; ++e) sum += (double)sorted_d[wid][e];
+      si.score[t] = (float)(sum / (double)k);
+    }
+    return __uint_as_float(T);
   };
   // with a split series only the lists of this call's strips exist
   const bool own = strip >= w.part_lo && strip < w.part_hi;
@@ -497,11 +657,15 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     if (n <= kMergeCap) break;
     // overflow: the k-th smallest of the buffered (valid, distinct) candidates is a
     // tighter bound; gather again under it
-    thr = select(kMergeCap);
+    thr = select_k(kMergeCap, false);
   }
   // final selection, written in (distance, index) order; if ties at the bound keep
   // the candidate set larger than the buffer, scan the lists directly each round
   const bool direct = n > kMergeCap;
+  if (!direct) {
+    select_k(n, true);
+    return;
+  }
   float last_d = -CUDART_INF_F;
   int last_i = -1;
   double sum = 0.0;
@@ -594,9 +758,21 @@ cudaError_t launch_prep_split_series(const SeriesTable& sr, int rows, int D, int
                                      void* lo, double* norms, float* cval, cudaStream_t st,
                                      int r_lo) {
   if (rows <= r_lo) return cudaSuccess;
-  const int blocks = (rows - r_lo + 7) / 8;
   __nv_bfloat16* h = static_cast<__nv_bfloat16*>(hi);
   __nv_bfloat16* l = static_cast<__nv_bfloat16*>(lo);
+  if (groups <= 16) {
+    // few groups per row: several rows per warp
+    const int per_block = 8 * (32 / groups);
+    const int nb = (rows - r_lo + per_block - 1) / per_block;
+    if (correct)
+      prep_split_small_kernel<true><<<nb, 256, 0, st>>>(sr, r_lo, rows, D, emb, groups, mu, wts,
+                                                        h, l, norms, cval);
+    else
+      prep_split_small_kernel<false><<<nb, 256, 0, st>>>(sr, r_lo, rows, D, emb, groups, mu, wts,
+                                                         h, l, norms, cval);
+    return cudaGetLastError();
+  }
+  const int blocks = (rows - r_lo + 7) / 8;
   // the embedded form (values of several days per row) maps a value to its grid point
   // by a division; the plain form needs none
   if (correct && emb > 1)
