@@ -104,7 +104,7 @@ typedef enum {
                                         operand row per trajectory (its L days, Eq. 1, L*D values)
                                         so that one Gram entry is the whole window sum of Eq. 2
                                         (L times the contraction, no diagonal sums); 2 never;
-                                        0 (default) when L*D <= 1024, the small-grid form (Sec. 5:
+                                        0 (default) when L*D <= 1536, the small-grid form (Sec. 5:
                                         fields reduced to a few dozen principal components) */
   TRAKNN_OPT_EPI_GROUPS = 14         /* tensor-core paths: 1 keeps one epilogue warpgroup; 0
                                         (default) uses two at L = 1 (embedded operands included)

@@ -573,7 +573,7 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
 // Trajectory-embedded operands for a single-series tensor-core call: automatic for
 // small grids, where the fixed per-chunk cost of the epilogue (staging, window sums)
 // and not the contraction decides the time, so L times the Gram work costs little.
-constexpr int64_t kEmbedAutoMaxLD = 1024;    // automatic: L * D at most this
+constexpr int64_t kEmbedAutoMaxLD = 1536;    // automatic: L * D at most this
 constexpr int64_t kEmbedMaxLD = 1 << 20;     // forced: L * D at most this
 bool use_embedding(const traknn_ctx* h, int64_t D, int L) {
   if (L < 2 || h->embed == 2) return false;
