@@ -322,7 +322,8 @@ traknn_status traknn_profile_read(traknn_handle handle, float* ms, int max_n, in
 
 /* Event counters of the tensor-core kernel accumulated while TRAKNN_OPT_STATS was on
  * (diagnostics): [0] row-side list insertions, [1] column-side candidates,
- * [2] reserved (always 0), [3] non-empty column lists,
+ * [2] column lists with more than k candidates (the column's own thread keeps the
+ * k best), [3] non-empty column lists,
  * [4] 32-column chunks processed, [5] MMA-thread cycles waiting for a free
  * accumulator, [6] MMA-thread cycles waiting for operands, [7] MMA-thread cycles
  * in total; cycles of the first epilogue thread [8] waiting for a filled

@@ -178,7 +178,7 @@ class Handle:
 
     def stats_read(self):
         """Kernel event counters since the last read (TRAKNN_OPT_STATS)."""
-        names = ["row_inserts", "col_emits", "reserved", "col_lists", "chunks",
+        names = ["row_inserts", "col_emits", "col_full", "col_lists", "chunks",
                  "mma_wait_tmem", "mma_wait_full", "mma_cycles", "epi_wait_acc",
                  "epi_tile_head", "epi_stage", "epi_bar1", "epi_scan", "epi_col", "epi_cycles"]
         buf = (ctypes.c_uint64 * len(names))()

@@ -245,7 +245,7 @@ inline size_t tc_scratch_bytes(int num_ctas) {
 enum : int {
   kStatRowInserts = 0,     // row-side list insertions
   kStatColEmits = 1,       // column-side candidates handed to a column
-  kStatReserved = 2,       // reserved (always 0)
+  kStatColFull = 2,        // column lists with more than k candidates (k best kept)
   kStatColLists = 3,       // non-empty column lists written
   kStatChunks = 4,         // 32-column chunks processed
   kStatMmaWaitTmem = 5,    // MMA-thread cycles spent waiting for a free accumulator

@@ -831,6 +831,7 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
             }
             if (tk_in(li * cpitch, w.col_ints, a.err)) w.col_rec[li * cpitch] = min(ne, us.k);
             cnt[3] += ne > 0;
+            cnt[2] += ne > us.k;  // lists kept by this thread's insertion
           }
           // the column side read other rows' Gram values: keep them until it is done
           if (colrange) ptx::named_bar_sync(bar, kEpiThreads);
@@ -880,7 +881,7 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
       lap(6);
       for (int i = 0; i < 6; ++i) atomicAdd(w.stats + kStatEpiWaitAcc + i, (unsigned long long)ph[i]);
       atomicAdd(w.stats + kStatEpiCycles, (unsigned long long)(clock64() - e_start));
-      atomicAdd(w.stats + kStatReserved, (unsigned long long)fold_cycles);
+      atomicAdd(w.stats + kStatEpiStage, (unsigned long long)fold_cycles);
     }
   }
 
