@@ -136,3 +136,53 @@ def test_invalid_neighbour_index_is_reported(tk):
     h = tk.get_handle()
     tk.score_backward(X, 3, 2, idx, torch.ones(48, device="cuda"))
     assert h.sync_status() == 1
+
+
+def test_days_with_many_incidences(tk):
+    """Neighbour lists with hub trajectories: the days near trajectory 500 (chosen by
+    1,500 trajectories) have between 512 and 4,096 incidences and are merged by a whole
+    CTA; the days after 2,000 and 2,001 (chosen by every trajectory) have more than
+    4,096 and list their incidences unmerged. Both against the oracle, and bitwise
+    reproducible."""
+    import torch
+    N, L, k = 3000, 5, 4
+    M = N - L + 1
+    X, _ = make_slp_like(N, 4, 5, seed=7)
+    t = np.arange(M)
+    idx = np.stack([np.where(t < 1500, 500, (t + 11) % M), np.full(M, 2000), np.full(M, 2001),
+                    (t + 5) % M], axis=1).astype(np.int32)
+    g = np.random.default_rng(3).uniform(0.5, 1.5, M)
+    Xd = torch.from_numpy(X).cuda()
+    gd = torch.from_numpy(g.astype(np.float32)).cuda()
+    idd = torch.from_numpy(idx).cuda()
+    d1 = tk.score_backward(Xd, L, k, idd, gd)
+    d2 = tk.score_backward(Xd, L, k, idd, gd)
+    torch.cuda.synchronize()
+    assert tk.get_handle().sync_status() == 0
+    assert torch.equal(d1, d2)
+    ref = oracle.score_grad(X, L, k, idx, g.astype(np.float32).astype(np.float64))
+    _assert_close(d1.cpu().numpy(), ref, 1e-5)
+
+
+@pytest.mark.parametrize("D", [64, 54])
+def test_load_forms_agree_bitwise(tk, D):
+    """The gather loads four grid points per thread as one 16-byte load (D a multiple
+    of 4, aligned rows), as two 8-byte loads, or one point per thread, depending on D
+    and the alignment of X: a copy of X placed 4 or 8 bytes past an aligned address
+    takes the other forms, with the same arithmetic and so the same bits."""
+    import torch
+    N, L, k, e = 400, 5, 8, 4
+    X, _ = make_slp_like(N, 8, D // 8, seed=D) if D % 8 == 0 else make_slp_like(N, 6, 9, seed=D)
+    assert X.shape[1] == D
+    Xd = torch.from_numpy(X).cuda()
+    idx, _, _ = tk.knn_scores(Xd, L, k, e)
+    g = torch.linspace(0.5, 1.5, N - L + 1, device="cuda")
+    ref = tk.score_backward(Xd, L, k, idx, g)
+    for shift in (1, 2):
+        buf = torch.empty(N * D + shift, device="cuda")
+        Xs = buf[shift:].view(N, D)
+        Xs.copy_(Xd)
+        got = tk.score_backward(Xs, L, k, idx, g)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), shift
+    assert tk.get_handle().sync_status() == 0
