@@ -203,6 +203,10 @@ struct TcWork {
   // one 16-byte load gives the count and the first entry.
   int32_t* col_rec;
   long long col_ints;       // ints of col_rec (index checks of the debug build)
+  // [stacked rows][mask_words] bit s of a row's mask: the column list of strip s for
+  // that row (as a column) is non-empty; only those lists have a record written
+  unsigned int* col_mask;
+  int mask_words;
   long long part_ints;      // entries of each row-side list array (likewise)
   unsigned int* thr;        // [stacked rows] bit patterns of an upper bound of each row's k-th distance
   int* counter;             // next unit to hand out (zero before the launch)

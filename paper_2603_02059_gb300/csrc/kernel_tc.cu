@@ -712,10 +712,14 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
               }
             }
             const float lthr = list.threshold();
+            // a row candidate has D < lthr and D <= thr_row, i.e. D <= rthr (the float
+            // below lthr when lthr > 0; none when lthr is 0)
+            const float rthr =
+                fminf(lthr > 0.f ? __uint_as_float(__float_as_uint(lthr) - 1u) : -1.f, thr_row);
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
               c[x] = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);  // D(t, j0 + x)
-              cand |= (c[x] < lthr && c[x] <= thr_row ? 1u : 0u) << x;
+              cand |= (c[x] <= rthr ? 1u : 0u) << x;
               ccand |= (c[x] <= tv[x] ? 1u : 0u) << x;
             }
             cand &= valid;
@@ -829,7 +833,12 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
               if (tk_in(us.out_base + j, a.out_rows, a.err))
                 publish_bound(w.thr + us.out_base + j, Cld[(us.k - 1) * 32 + cx]);
             }
-            if (tk_in(li * cpitch, w.col_ints, a.err)) w.col_rec[li * cpitch] = min(ne, us.k);
+            if (ne > 0) {  // an empty list gets no record: its mask bit stays clear
+              if (tk_in(li * cpitch, w.col_ints, a.err)) w.col_rec[li * cpitch] = min(ne, us.k);
+              const long long mi = (long long)(us.out_base + j) * w.mask_words + (us.strip >> 5);
+              if (tk_in(mi, (long long)a.out_rows * w.mask_words, a.err))
+                atomicOr(w.col_mask + mi, 1u << (us.strip & 31));
+            }
             cnt[3] += ne > 0;
             cnt[2] += ne > us.k;  // lists kept by this thread's insertion
           }

@@ -454,6 +454,15 @@ __global__ void merge_parts_kernel(const int32_t* __restrict__ pidx,
 constexpr int kMergeWarps = 8;
 constexpr int kMergeCap = 256;
 
+// Bits [lo, hi) of a 32-bit word (empty when hi <= lo).
+__device__ __forceinline__ uint32_t bit_range32(int lo, int hi) {
+  lo = max(lo, 0);
+  hi = min(hi, 32);
+  if (hi <= lo) return 0u;
+  const uint32_t w = (hi - lo >= 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
+  return w << lo;
+}
+
 __device__ __forceinline__ bool key_less(float d1, int i1, float d2, int i2) {
   return d1 < d2 || (d1 == d2 && i1 < i2);
 }
@@ -623,30 +632,56 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
     }
     if (w.sym) {
-      // column lists (not sorted): the first 32 bytes of a record (one sector, two
-      // loads in flight together) hold its count and three entries
-      constexpr int kColBatch = 1;
-      for (int sb = s2_lo + lane; sb < s2_hi; sb += 32 * kColBatch) {
-        int4 h0[kColBatch], h1[kColBatch];
-        long long ri[kColBatch];
+      // column lists (not sorted) from the strips above this row: only the non-empty
+      // ones (their bit set in the row's mask) have a record. The set bits are numbered
+      // across the mask words (a prefix sum over the lanes' words), each lane takes one
+      // per round, and reads the first 32 bytes of its record (two loads in flight
+      // together): the count and three entries
+      const long long mrow = (long long)r * w.mask_words;
+      const long long mlim = (long long)out_rows * w.mask_words;
+      for (int wb0 = 0; wb0 < w.mask_words; wb0 += 32) {
+        const int wb = wb0 + lane;
+        uint32_t m = 0;
+        if (wb < w.mask_words && tk_in(mrow + wb, mlim, err))
+          m = __ldg(w.col_mask + mrow + wb) & bit_range32(s2_lo - 32 * wb, s2_hi - 32 * wb);
+        const int pc = __popc(m);
+        int incl = pc;
 #pragma unroll
-        for (int u = 0; u < kColBatch; ++u) {
-          const int s2 = sb + 32 * u;
-          ri[u] = s2 < s2_hi && tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)
-                      ? collist(s2) * cp : -1;
-          const int4* r4 = reinterpret_cast<const int4*>(w.col_rec + (ri[u] >= 0 ? ri[u] : 0));
-          h0[u] = ri[u] >= 0 ? __ldg(r4) : make_int4(0, 0, 0, 0);
-          h1[u] = ri[u] >= 0 ? __ldg(r4 + 1) : make_int4(0, 0, 0, 0);
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
         }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - pc;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+          const int e = e0 + lane;
+          // the word holding set bit e: the last lane whose prefix is <= e
+          int wl = 0;
 #pragma unroll
-        for (int u = 0; u < kColBatch; ++u) {
-          const int nn = tk_in(h0[u].x, ks + 1, err) ? h0[u].x : 0;  // count <= k
-          if (nn > 0 && __int_as_float(h0[u].w) <= thr) push(__int_as_float(h0[u].w), h0[u].z);
-          if (nn > 1 && __int_as_float(h1[u].y) <= thr) push(__int_as_float(h1[u].y), h1[u].x);
-          if (nn > 2 && __int_as_float(h1[u].w) <= thr) push(__int_as_float(h1[u].w), h1[u].z);
+          for (int step = 16; step > 0; step >>= 1) {
+            const int x = __shfl_sync(0xffffffffu, excl, wl + step);
+            if (x <= e) wl += step;
+          }
+          const uint32_t mw = __shfl_sync(0xffffffffu, m, wl);
+          const int want = e - __shfl_sync(0xffffffffu, excl, wl);  // rank within the word
+          if (e >= total) continue;
+          int b0 = 0;  // the want-th set bit of mw: smallest b with popc(mw & bits 0..b) > want
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1)
+            if (__popc(mw & (0xFFFFFFFFu >> (31 - (b0 + step - 1)))) <= want) b0 += step;
+          const int s2 = 32 * (wb0 + wl) + b0;
+          const long long ri =
+              tk_in(collist(s2) * cp + cp - 1, w.col_ints, err) ? collist(s2) * cp : -1;
+          if (ri < 0) continue;
+          const int4* r4 = reinterpret_cast<const int4*>(w.col_rec + ri);
+          const int4 h0 = __ldg(r4), h1 = __ldg(r4 + 1);
+          const int nn = tk_in(h0.x, ks + 1, err) ? h0.x : 0;  // count <= k
+          if (nn > 0 && __int_as_float(h0.w) <= thr) push(__int_as_float(h0.w), h0.z);
+          if (nn > 1 && __int_as_float(h1.y) <= thr) push(__int_as_float(h1.y), h1.x);
+          if (nn > 2 && __int_as_float(h1.w) <= thr) push(__int_as_float(h1.w), h1.z);
           for (int p = 3; p < nn; ++p) {
-            const int2 e = __ldg(reinterpret_cast<const int2*>(w.col_rec + ri[u]) + 1 + p);
-            if (__int_as_float(e.y) <= thr) push(__int_as_float(e.y), e.x);
+            const int2 en = __ldg(reinterpret_cast<const int2*>(w.col_rec + ri) + 1 + p);
+            if (__int_as_float(en.y) <= thr) push(__int_as_float(en.y), en.x);
           }
         }
       }
@@ -692,6 +727,10 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
       }
       if (w.sym) {
         for (int s2 = s2_lo + lane; s2 < s2_hi; s2 += 32) {
+          const long long mi = (long long)r * w.mask_words + (s2 >> 5);
+          if (!tk_in(mi, (long long)out_rows * w.mask_words, err) ||
+              !((__ldg(w.col_mask + mi) >> (s2 & 31)) & 1u))
+            continue;  // an empty list has no record
           if (!tk_in(collist(s2) * cp + cp - 1, w.col_ints, err)) continue;
           const int2* rec = reinterpret_cast<const int2*>(w.col_rec + collist(s2) * cp);
           const int nn = tk_in(rec[0].x, ks + 1, err) ? rec[0].x : 0;

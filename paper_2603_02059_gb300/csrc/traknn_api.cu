@@ -45,6 +45,7 @@ struct TcPlan {
   // they can run while the days before phase_strip are still being copied in.
   int phase_strip = 0, nunits_a = 0, nband_a = 0;
   int egroups = 1;  // epilogue groups of the fused kernel; each writes its own row lists
+  int mask_words = 1;  // 32-bit words per row of the non-empty column-list masks
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
@@ -183,6 +184,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
   long long part_base = 0, col_base = 0;
   p.kmax = 0;
   p.Lmax = 1;
+  p.mask_words = 1;
   p.table.n = B;
   int Lshare = 1;
   for (int b = 0; b < B; ++b) Lshare = std::max(Lshare, sd[b].L);
@@ -193,6 +195,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     const int R = kTileRows - (Lg - 1);
     const int step = kTileCols - (Lg - 1);
     const int strips = (M + R - 1) / R;
+    p.mask_words = std::max(p.mask_words, (strips + 31) / 32);
     const int cols = shared ? step : cols_opt > 0 ? cols_opt : tiles * kTileCols - (Lg - 1);
     // row-side list slots per trajectory row: one per column range and epilogue group
     const int slots = (M + cols - 1) / cols * egroups;
@@ -302,6 +305,7 @@ struct TcBuffers {
   int32_t* part_i;
   unsigned int* thr;
   int32_t* col_rec;
+  unsigned int* col_mask;
   int* counter;
   float* scratch;
   float* pscore;  // [out_rows] scores of partial lists (split series), not returned
@@ -333,6 +337,8 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
   b.thr = reinterpret_cast<unsigned int*>(take((size_t)p.out_rows * sizeof(unsigned int)));
   b.col_rec = reinterpret_cast<int32_t*>(
       take((size_t)p.col_lists * col_pitch((int)ks) * sizeof(int32_t)));
+  b.col_mask = reinterpret_cast<unsigned int*>(
+      take((size_t)p.out_rows * p.mask_words * sizeof(unsigned int)));
   b.counter = reinterpret_cast<int*>(take(256));
   b.scratch = reinterpret_cast<float*>(take(tc_scratch_bytes(num_ctas)));
   b.pscore = reinterpret_cast<float*>(take((size_t)p.out_rows * sizeof(float)));
@@ -440,6 +446,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   w.sym = h->sym;
   w.col_rec = b.col_rec;
   w.col_ints = p.col_lists * col_pitch(w.kstride);
+  w.col_mask = b.col_mask;
+  w.mask_words = p.mask_words;
   w.part_ints = p.part_lists * w.kstride;
   w.thr = b.thr;
   w.counter = b.counter;
@@ -456,6 +464,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
                                     b.norms, b.cval, s));
   TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s));
   TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
+  TRY_CUDA(cudaMemsetAsync(b.col_mask, 0,
+                           (size_t)p.out_rows * p.mask_words * sizeof(unsigned int), s));
   TRY_CUDA(cudaMemsetAsync(b.counter, 0, 2 * sizeof(int), s));
   const int slot = h->ev_head;
   if (record_events) TRY_CUDA(cudaEventRecord(h->ev_start[slot], s));
@@ -526,6 +536,8 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
   w.sym = h->sym;
   w.col_rec = b.col_rec;
   w.col_ints = p.col_lists * col_pitch(w.kstride);
+  w.col_mask = b.col_mask;
+  w.mask_words = p.mask_words;
   w.part_ints = p.part_lists * w.kstride;
   w.thr = b.thr;
   w.write_lists = 1;
@@ -553,6 +565,8 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
                                     b.hi, b.lo, b.norms, b.cval, s, h0));
   TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s, h0));
   TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
+  TRY_CUDA(cudaMemsetAsync(b.col_mask, 0,
+                           (size_t)p.out_rows * p.mask_words * sizeof(unsigned int), s));
   TRY_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
   TRY_CUDA(fused(p.nunits, p.nband_a, 1, true));
   TRY_CUDA(fused(0, p.nunits_a, 0, false));
@@ -1115,7 +1129,6 @@ traknn_status traknn_score_backward(traknn_handle h, const float* X, int64_t N, 
   if (N < 1 || D < 1 || L < 1 || L > N || k < 1) return TRAKNN_ERR_INVALID_ARG;
   if (N > INT_MAX / 2 || D > INT_MAX / 2) return TRAKNN_ERR_INVALID_ARG;
   if (L > TRAKNN_MAX_L || k > TRAKNN_MAX_K) return TRAKNN_ERR_UNSUPPORTED;
-  const int M = (int)(N - L + 1);
   TRY_ST(ensure_buffer(h, &h->adj, &h->adj_bytes, adjoint_workspace_bytes((int)N, L, k)));
   int launches = 0;
   if (h->weights && h->weights_D != D) return TRAKNN_ERR_INVALID_ARG;
