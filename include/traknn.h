@@ -70,8 +70,8 @@ typedef enum {
 typedef enum {
   TRAKNN_OPT_PRECISION = 0,          /* a traknn_precision value (default SPLIT_BF16) */
   TRAKNN_OPT_CENTER = 1,             /* 1: subtract the per-grid-point mean over days before the
-                                        Gram (days 0, s, 2s, ..., at most 4,096 of them; exact by
-                                        the offset invariance of Eq. 2 whatever the mean; default 1) */
+                                        Gram (the last 4,096 days, or all when fewer; exact by the
+                                        offset invariance of Eq. 2 whatever the mean; default 1) */
   TRAKNN_OPT_COL_CHUNKS = 2,         /* column chunks per row strip, 0 = automatic */
   TRAKNN_OPT_WAIT_LIMIT_MS = 3,      /* limit of every device spin-wait in ms (default 2000) */
   TRAKNN_OPT_DEBUG_WITHHOLD = 4,     /* test hook: 1 makes the tensor-core kernel's producer withhold

@@ -27,13 +27,11 @@ constexpr int kErrTimeout = 5;
 constexpr int kErrInvalidArg = 1;
 // Column-mean partial sums use this many row slices (fixed order => deterministic).
 constexpr int kMeanSlices = 64;
-// Centring: the per-grid-point mean over days 0, s, 2s, ... (at most kMeanDays days).
+// Centring: the per-grid-point mean over the last kMeanDays days (all days when there
+// are fewer): days [mean_first(N), N). A host-buffer call copies those days in first.
 constexpr int kMeanDays = 4096;
-__host__ __device__ inline int mean_stride(int N) { return (N + kMeanDays - 1) / kMeanDays; }
-__host__ __device__ inline int mean_days(int N) {
-  const int s = mean_stride(N);
-  return (N + s - 1) / s;
-}
+__host__ __device__ inline int mean_days(int N) { return N < kMeanDays ? N : kMeanDays; }
+__host__ __device__ inline int mean_first(int N) { return N - mean_days(N); }
 // Status word value of the debug build's index checks (TRAKNN_ERR_BOUNDS).
 constexpr int kErrBounds = 9;
 

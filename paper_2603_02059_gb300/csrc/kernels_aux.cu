@@ -16,20 +16,20 @@ namespace traknn {
 namespace {
 
 // The centring offset only has to be one fixed field subtracted from every day (any
-// value keeps Eq. 2 exact); the mean over days 0, s, 2s, ... (at most kMeanDays of
-// them) is close enough to the full mean to shrink the Gram values as well, and costs
-// a small fraction of a pass over X.
+// value keeps Eq. 2 exact); the mean over the last kMeanDays days is close enough to
+// the full mean to shrink the Gram values as well, costs a small fraction of a pass
+// over X, and lies in the first part of X a host-buffer call copies in.
 
 // Column sums of the sampled days over fixed slices (fixed summation order:
 // deterministic).
 __global__ void col_partial_kernel(const float* __restrict__ X, int N, int D, float* partial) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D) return;
-  const int stride = mean_stride(N), ns = mean_days(N);
+  const int first = mean_first(N), ns = mean_days(N);
   const int per = (ns + kMeanSlices - 1) / kMeanSlices;
   const int r0 = blockIdx.y * per, r1 = min(ns, r0 + per);
   float acc = 0.f;
-  for (int i = r0; i < r1; ++i) acc += X[(size_t)i * stride * D + p];
+  for (int i = r0; i < r1; ++i) acc += X[(size_t)(first + i) * D + p];
   partial[(size_t)blockIdx.y * D + p] = acc;
 }
 
@@ -97,11 +97,11 @@ __global__ void col_partial_series_kernel(const __grid_constant__ SeriesTable st
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D) return;
   const SeriesInfo& si = st.s[blockIdx.z];
-  const int stride = mean_stride(si.N), ns = mean_days(si.N);
+  const int first = mean_first(si.N), ns = mean_days(si.N);
   const int per = (ns + kMeanSlices - 1) / kMeanSlices;
   const int r0 = blockIdx.y * per, r1 = min(ns, r0 + per);
   float acc = 0.f;
-  for (int i = r0; i < r1; ++i) acc += si.X[(size_t)i * stride * D + p];
+  for (int i = r0; i < r1; ++i) acc += si.X[(size_t)(first + i) * D + p];
   partial[((size_t)blockIdx.z * kMeanSlices + blockIdx.y) * D + p] = acc;
 }
 

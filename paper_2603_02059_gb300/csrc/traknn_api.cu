@@ -40,19 +40,19 @@ struct TcPlan {
   long long part_lists = 0, col_lists = 0;
   int emb = 1;  // days per operand row (trajectory-embedded operands when > 1)
   int part_lo = 0, part_hi = INT_MAX;  // strips evaluated (one part of a split series)
-  // Two phases (host-buffer calls, one series): strips >= phase_strip first (their
-  // main units, then band units, are the first nunits_a / nband_a of each list), so
-  // they can run while the days before phase_strip are still being copied in.
-  int phase_strip = 0, nunits_a = 0, nband_a = 0;
+  // Host-buffer calls in phases (one series): phase q runs the strips
+  // [pstrip[q+1], pstrip[q]) (pstrip[0] = strips, the last 0), the later strips first,
+  // each as soon as the days it reads (from pstrip[q+1] * R on: upper triangle) are in.
+  // Its main units are units[pu[q] .. pu[q+1]), its band units units[pb[q] .. pb[q+1])
+  // (stored after every main unit). One phase: pstrip empty, pu = {0, nunits},
+  // pb = {nunits, nunits + nband}.
+  std::vector<int> pstrip, pu, pb;
   int egroups = 1;  // epilogue groups of the fused kernel; each writes its own row lists
   int mask_words = 1;  // 32-bit words per row of the non-empty column-list masks
 };
 
 constexpr size_t kMaxGraphs = 16;  // captured launch sequences kept per handle
-// Host-buffer calls: the strips from this fraction of the series on run while the days
-// before them are copied in (the later strips hold less work: at the 75-year workload,
-// copy and compute of the two phases then overlap best).
-constexpr double kPhaseFrac = 0.55;
+constexpr int kMaxPhases = 8;      // phases of a host-buffer call
 
 struct GraphEntry {
   std::vector<int64_t> key;  // plan key, pointers and options
@@ -109,7 +109,8 @@ struct traknn_ctx {
   cudaStream_t cap_stream = nullptr;
   // host-buffer calls: copy stream and its events (created on first use)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_io_free = nullptr, ev_late_in = nullptr, ev_early_in = nullptr;
+  cudaEvent_t ev_io_free = nullptr;
+  cudaEvent_t ev_in[kMaxPhases] = {};  // the days of phase q are in
 };
 
 namespace {
@@ -174,12 +175,18 @@ inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
 // unit is one tile long and carries all B series (pad[0] = B), and the first series
 // (smallest L, most trajectories) defines the units' column ranges.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
-                int group_opt, bool shared, int part_lo, int part_hi, int phase_strip,
-                int egroups, TcPlan& p) {
+                int group_opt, bool shared, int part_lo, int part_hi,
+                const std::vector<int>& pstrip, int egroups, TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
-  std::vector<WorkUnit> band, later, later_band;  // the second phase's units
+  const int K = pstrip.empty() ? 1 : (int)pstrip.size() - 1;  // phases
+  auto phase_of = [&](int s) {
+    int q = 0;
+    while (q + 1 < K && s < pstrip[q + 1]) ++q;
+    return q;
+  };
+  std::vector<std::vector<WorkUnit>> mainq(K), bandq(K);  // units of each phase
   int row_base = 0, out_base = 0, strip_base = 0;
   long long part_base = 0, col_base = 0;
   p.kmax = 0;
@@ -232,9 +239,7 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
             int jlo = c * cols;
             const int jhi = std::min(M, (c + 1) * cols);
             if (sym) jlo = std::max(jlo, s * R);
-            if (jlo < jhi)
-              (phase_strip > 0 && s < phase_strip ? later : p.units)
-                  .push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
+            if (jlo < jhi) mainq[phase_of(s)].push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
           }
       }
       // band: two tiles of columns (2 kTileCols - (L-1) outputs) centred on the strip's rows
@@ -243,12 +248,11 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
         const int T0 = s * R;
         int jlo = std::max(0, T0 - bw);
         const int jhi = std::min(M, T0 + R + bw);
-        // first-phase band units stay clear of the days still being copied (a band
-        // only seeds bounds, from whatever candidates it holds)
-        if (phase_strip > 0 && s >= phase_strip) jlo = std::max(jlo, phase_strip * R);
-        if (jlo < jhi)
-          (phase_strip > 0 && s < phase_strip ? later_band : band)
-              .push_back(WorkUnit{b, s, jlo, jhi, 0, {nser, 0, 0}});
+        // a phase's band units stay clear of the days still being copied (a band only
+        // seeds bounds, from whatever candidates it holds)
+        const int q = phase_of(s);
+        if (K > 1) jlo = std::max(jlo, pstrip[q + 1] * R);
+        if (jlo < jhi) bandq[q].push_back(WorkUnit{b, s, jlo, jhi, 0, {nser, 0, 0}});
       }
     }
     if (!shared || b == B - 1) row_base += N;
@@ -259,15 +263,20 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
     p.kmax = std::max(p.kmax, k);
     p.Lmax = std::max(p.Lmax, L);
   }
-  p.phase_strip = phase_strip;
+  p.pstrip = pstrip;
   p.egroups = egroups;
-  p.nunits_a = (int)p.units.size();
-  p.nband_a = (int)band.size();
-  p.units.insert(p.units.end(), later.begin(), later.end());
-  band.insert(band.end(), later_band.begin(), later_band.end());
+  p.pu.assign(1, 0);
+  for (int q = 0; q < K; ++q) {
+    p.units.insert(p.units.end(), mainq[q].begin(), mainq[q].end());
+    p.pu.push_back((int)p.units.size());
+  }
   p.nunits = (int)p.units.size();
-  p.nband = (int)band.size();
-  p.units.insert(p.units.end(), band.begin(), band.end());
+  p.pb.assign(1, p.nunits);
+  for (int q = 0; q < K; ++q) {
+    p.units.insert(p.units.end(), bandq[q].begin(), bandq[q].end());
+    p.pb.push_back((int)p.units.size());
+  }
+  p.nband = (int)p.units.size() - p.nunits;
   p.rows = row_base;
   p.out_rows = out_base;
   p.part_lists = part_base;
@@ -350,8 +359,8 @@ TcBuffers tc_layout(const TcPlan& p, int64_t D, int num_ctas, char* base) {
 // and size the workspace. Must not run during a stream capture.
 traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int tiles,
                          bool shared, int emb, cudaStream_t s, TcBuffers* out,
-                         int part_lo = 0, int part_hi = INT_MAX, int phase_strip = 0,
-                         int group = 0) {
+                         int part_lo = 0, int part_hi = INT_MAX,
+                         const std::vector<int>& pstrip = {}, int group = 0) {
   if (group <= 0) group = h->group_strips;  // 0: the planner's default
   std::vector<int64_t> key = shape_key(sd, B, D, h);
   key.push_back(tiles);
@@ -360,7 +369,8 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   key.push_back(emb);
   key.push_back(part_lo);
   key.push_back(part_hi);
-  key.push_back(phase_strip);
+  key.push_back((int64_t)pstrip.size());
+  key.insert(key.end(), pstrip.begin(), pstrip.end());
   // two epilogue groups for L = 1 (small grids through embedded operands) when the
   // tile has one accumulation segment and the lists are short
   int Lmax = 1, kmax = 1;
@@ -375,8 +385,8 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   key.push_back(egroups);
   TcPlan& p = h->plan;
   if (p.key != key) {
-    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, group, shared, part_lo, part_hi,
-               phase_strip, egroups, p);
+    build_plan(sd, B, D, h->sym, h->unit_cols, tiles, group, shared, part_lo, part_hi, pstrip,
+               egroups, p);
     p.key = key;
     p.emb = emb;
     p.part_lo = part_lo;
@@ -491,22 +501,46 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
 }
 
 
-// The launch sequence of a host-buffer call in two phases (plan built with a phase
-// strip, one series): the days the centring mean samples and the days [h0, N) are
-// copied in first (event late_in on the copy stream), the other days [0, h0) after
-// them (early_in). Strips from phase_strip on read only days >= h0 = phase_strip * R
-// (upper triangle: columns j >= T0 of the strip), so their band and main units run
-// as soon as those days are in, while the copy of the earlier days continues; then the
-// earlier days are prepared and the remaining strips run; one merge follows. The
-// operands, and so every distance, are those of the one-phase sequence; only the
-// order of the work units differs.
+// Phases of a host-buffer call (tensor-core path, one series): strip boundaries
+// pstrip[0] = strips > pstrip[1] > ... > pstrip[K] = 0, phase q reading the days from
+// pstrip[q+1] R on; phase q starts once the fraction kPhaseDays[q] of the days (the
+// last ones) is in. Phase 0 holds at least the days the centring mean reads. With the
+// upper triangle the work a fraction F of the days unlocks is F^2 of the call, and it
+// is concentrated in few strips with few units each, so every phase ends with a tail
+// of idle SMs: a few large phases overlap the copy better than many small ones.
+// Empty when the series is too short to split.
+constexpr double kPhaseDays[] = {0.35};
+std::vector<int> phase_plan(int strips, int R, int64_t N) {
+  std::vector<int> ps;
+  if (strips < 8) return ps;
+  const int first = mean_first((int)N) / R;  // last boundary that keeps the mean's days
+  ps.push_back(strips);
+  for (double f : kPhaseDays) {
+    const int sb = std::min(first, (int)std::floor((1.0 - f) * (double)N / R));
+    if (sb < 2 || sb > ps.back() - 2) break;
+    ps.push_back(sb);
+  }
+  ps.push_back(0);
+  if (ps.size() <= 2) ps.clear();
+  return ps;
+}
+
+// The launch sequence of a host-buffer call in phases (plan built with phase
+// boundaries, one series). The days of phase q, [pstrip[q+1] R, pstrip[q] R) (phase 0:
+// up to N, including the days the centring mean reads), are copied in on the copy
+// stream in phase order, event in[q] after each. Phase q waits for its days, prepares
+// their operand rows and window sums, and runs its band and main units: strips from
+// pstrip[q+1] on read only days >= pstrip[q+1] R (upper triangle: columns j >= T0 of
+// the strip), so each phase runs while the copy of the earlier days continues. One
+// merge follows. The operands, and so every distance, are those of the one-phase
+// sequence; only the order of the work units differs.
 traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cudaStream_t s,
-                                cudaEvent_t late_in, cudaEvent_t early_in) {
+                                const cudaEvent_t* in) {
   const TcPlan& p = h->plan;
   const SeriesTable& sr = p.table;
   const SeriesInfo& si = sr.s[0];
   const int R = kTileRows - (si.L - 1);
-  const int h0 = p.phase_strip * R;
+  const int K = (int)p.pstrip.size() - 1;
   const size_t ub = align_up(p.units.size() * sizeof(WorkUnit), 256);
   const size_t cb = align_up(p.col_off.size() * sizeof(long long), 256);
   char* pd = static_cast<char*>(h->plan_dev);
@@ -558,29 +592,32 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
     ++h->launches;
     return launch_fused_tc(b.hi, b.lo, split, a, x, sr, h->sm_count, s);
   };
-  // phase 1: the later days
-  TRY_CUDA(cudaStreamWaitEvent(s, late_in, 0));
-  TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
-  TRY_CUDA(launch_prep_split_series(sr, p.rows, (int)D, 1, b.Dp / 64, split, b.mu, h->weights,
-                                    b.hi, b.lo, b.norms, b.cval, s, h0));
-  TRY_CUDA(launch_window_series(sr, p.out_rows, b.norms, b.W, s, h0));
-  TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
-  TRY_CUDA(cudaMemsetAsync(b.col_mask, 0,
-                           (size_t)p.out_rows * p.mask_words * sizeof(unsigned int), s));
-  TRY_CUDA(cudaMemsetAsync(b.counter, 0, 4 * sizeof(int), s));
-  TRY_CUDA(fused(p.nunits, p.nband_a, 1, true));
-  TRY_CUDA(fused(0, p.nunits_a, 0, false));
-  // phase 2: the earlier days
-  TRY_CUDA(cudaStreamWaitEvent(s, early_in, 0));
-  TRY_CUDA(launch_prep_split_series(sr, h0, (int)D, 1, b.Dp / 64, split, b.mu, h->weights, b.hi,
-                                    b.lo, b.norms, b.cval, s, 0));
-  TRY_CUDA(launch_window_series(sr, std::min(h0, p.out_rows), b.norms, b.W, s, 0));
-  TRY_CUDA(fused(p.nunits + p.nband_a, p.nband - p.nband_a, 3, true));
-  TRY_CUDA(fused(p.nunits_a, p.nunits - p.nunits_a, 2, false));
+  for (int q = 0; q < K; ++q) {
+    const int lo = p.pstrip[q + 1] * R;                      // first day (and row) of phase q
+    const int hi = q == 0 ? p.rows : p.pstrip[q] * R;        // rows prepared by phase q
+    const int ohi = q == 0 ? p.out_rows : std::min(hi, p.out_rows);
+    TRY_CUDA(cudaStreamWaitEvent(s, in[q], 0));
+    if (q == 0) {
+      TRY_CUDA(launch_col_mean_series(sr, (int)D, b.partial, b.mu, h->center != 0, s));
+      TRY_CUDA(cudaMemsetAsync(b.thr, 0x7F, (size_t)p.out_rows * sizeof(unsigned int), s));
+      TRY_CUDA(cudaMemsetAsync(b.col_mask, 0,
+                               (size_t)p.out_rows * p.mask_words * sizeof(unsigned int), s));
+      TRY_CUDA(cudaMemsetAsync(b.counter, 0, 2 * K * sizeof(int), s));
+      h->launches += h->center ? 2 : 1;
+    }
+    // window sums of rows [lo, ohi) read day norms up to ohi + L - 2: prepared now or
+    // by an earlier phase
+    TRY_CUDA(launch_prep_split_series(sr, hi, (int)D, 1, b.Dp / 64, split, b.mu, h->weights,
+                                      b.hi, b.lo, b.norms, b.cval, s, lo));
+    TRY_CUDA(launch_window_series(sr, ohi, b.norms, b.W, s, lo));
+    h->launches += (hi > lo ? 1 : 0) + (ohi > lo ? 1 : 0);
+    TRY_CUDA(fused(p.pb[q], p.pb[q + 1] - p.pb[q], 2 * q + 1, true));
+    TRY_CUDA(fused(p.pu[q], p.pu[q + 1] - p.pu[q], 2 * q, false));
+  }
   w.nunits = p.nunits;
   w.counter = b.counter;
   TRY_CUDA(launch_merge_tc(a, w, sr, s));
-  h->launches += (h->center ? 2 : 1) + 4 + 1;
+  h->launches += 1;
   return TRAKNN_OK;
 }
 
@@ -634,7 +671,7 @@ traknn_status pick_shape(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   for (int cand_g : groups)
     for (int cand_t : {4, 8, 16}) {
       TcBuffers buf;
-      TRY_ST(prepare_tc(h, sd, B, D, cand_t, false, 1, s, &buf, 0, INT_MAX, 0, cand_g));
+      TRY_ST(prepare_tc(h, sd, B, D, cand_t, false, 1, s, &buf, 0, INT_MAX, {}, cand_g));
       TRY_ST(enqueue_tc(h, buf, D, s, false));  // warm-up
       TRY_CUDA(cudaEventRecord(e0, s));
       TRY_ST(enqueue_tc(h, buf, D, s, false));
@@ -666,7 +703,7 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
   const bool whole = part_lo == 0 && part_hi == INT_MAX;
   if (!shared && emb == 1 && whole) TRY_ST(pick_shape(h, sd, B, D, s, &tiles, &group));
   TcBuffers buf;
-  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi, 0, group));
+  TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi, {}, group));
   h->last_tiles = tiles;
   h->last_group = group > 0 ? group : (h->group_strips > 0 ? h->group_strips : 19);
   if (!graph) return enqueue_tc(h, buf, D, s, h->profile != 0);
@@ -783,7 +820,8 @@ traknn_status traknn_destroy(traknn_handle h) {
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
-  for (cudaEvent_t ev : {h->ev_io_free, h->ev_late_in, h->ev_early_in})
+  if (h->ev_io_free) cudaEventDestroy(h->ev_io_free);
+  for (cudaEvent_t ev : h->ev_in)
     if (ev) cudaEventDestroy(ev);
   if (h->ws) cudaFree(h->ws);
   if (h->tcws) cudaFree(h->tcws);
@@ -1061,55 +1099,39 @@ traknn_status traknn_knn_scores_host(traknn_handle h, const float* Xh, int64_t N
   int32_t* idx_d = reinterpret_cast<int32_t*>(io + xb);
   float* dist_d = reinterpret_cast<float*>(io + xb + ib);
   float* score_d = reinterpret_cast<float*>(io + xb + ib + db);
-  // Two phases when the series has enough strips: the copy of the later days, then of
-  // the earlier ones, on the copy stream; the strips of the later days start as soon
-  // as their days are in (see enqueue_tc_phased)
+  // Phases when the series has enough strips: its days are copied in on the copy
+  // stream from the last ones back, and the strips whose days are in start while the
+  // copy of the earlier days continues (see phase_plan and enqueue_tc_phased)
   const int R = kTileRows - (L - 1);
   const int strips = (int)((M + R - 1) / R);
-  const int phase_strip = (int)(kPhaseFrac * strips + 0.5);
-  const bool phased = h->precision != TRAKNN_PREC_FP32 && h->sym && !use_embedding(h, D, L) &&
-                      (!h->weights || h->weights_D == D) && strips >= 8 && tc_available();
-  if (!phased) {
+  const bool tc_form = h->precision != TRAKNN_PREC_FP32 && h->sym && !use_embedding(h, D, L) &&
+                       (!h->weights || h->weights_D == D) && tc_available();
+  const std::vector<int> ps = tc_form ? phase_plan(strips, R, N) : std::vector<int>();
+  if (ps.empty()) {
     TRY_CUDA(cudaMemcpyAsync(Xd, Xh, (size_t)N * D * sizeof(float), cudaMemcpyHostToDevice, s));
     TRY_ST(traknn_knn_scores(h, Xd, N, D, L, k, e, idx_d, dist_d, score_d, stream));
   } else {
     if (!h->copy_stream) {
       TRY_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
       TRY_CUDA(cudaEventCreateWithFlags(&h->ev_io_free, cudaEventDisableTiming));
-      TRY_CUDA(cudaEventCreateWithFlags(&h->ev_late_in, cudaEventDisableTiming));
-      TRY_CUDA(cudaEventCreateWithFlags(&h->ev_early_in, cudaEventDisableTiming));
+      for (cudaEvent_t& ev : h->ev_in)
+        TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     const HostSeries sd{Xd, N, L, k, e, idx_d, dist_d, score_d};
     TcBuffers buf;
-    TRY_ST(prepare_tc(h, &sd, 1, D, 8, false, 1, s, &buf, 0, INT_MAX, phase_strip));
-    const int64_t h0 = (int64_t)phase_strip * R;
+    TRY_ST(prepare_tc(h, &sd, 1, D, 8, false, 1, s, &buf, 0, INT_MAX, ps));
     const size_t row = (size_t)D * sizeof(float);
-    const int64_t ms = mean_stride((int)N);          // centring samples days 0, ms, 2ms, ...
-    const int64_t ns_e = (h0 + ms - 1) / ms;         // sampled days before h0
     const cudaStream_t cs = h->copy_stream;
     // the staging buffer is rewritten only after earlier work on `stream` is done
     TRY_CUDA(cudaEventRecord(h->ev_io_free, s));
     TRY_CUDA(cudaStreamWaitEvent(cs, h->ev_io_free, 0));
-    // 1. the sampled days before h0 (one strided copy), 2. the days [h0, N)
-    TRY_CUDA(cudaMemcpy2DAsync(Xd, ms * row, Xh, ms * row, row, (size_t)ns_e,
+    for (int q = 0; q + 1 < (int)ps.size(); ++q) {
+      const int64_t lo = (int64_t)ps[q + 1] * R, hi = q == 0 ? N : (int64_t)ps[q] * R;
+      TRY_CUDA(cudaMemcpyAsync(Xd + lo * D, Xh + lo * D, (size_t)(hi - lo) * row,
                                cudaMemcpyHostToDevice, cs));
-    TRY_CUDA(cudaMemcpyAsync(Xd + h0 * D, Xh + h0 * D, (size_t)(N - h0) * row,
-                             cudaMemcpyHostToDevice, cs));
-    TRY_CUDA(cudaEventRecord(h->ev_late_in, cs));
-    // 3. the other days before h0: full gaps between sampled days (strided), then the
-    // last, shorter gap
-    if (ms > 1) {
-      const int64_t full = (h0 - 1) / ms;  // gaps [i ms + 1, (i+1) ms) inside [0, h0)
-      if (full > 0)
-        TRY_CUDA(cudaMemcpy2DAsync(Xd + D, ms * row, Xh + D, ms * row, (ms - 1) * row,
-                                   (size_t)full, cudaMemcpyHostToDevice, cs));
-      const int64_t r0 = full * ms + 1;
-      if (r0 < h0)
-        TRY_CUDA(cudaMemcpyAsync(Xd + r0 * D, Xh + r0 * D, (size_t)(h0 - r0) * row,
-                                 cudaMemcpyHostToDevice, cs));
+      TRY_CUDA(cudaEventRecord(h->ev_in[q], cs));
     }
-    TRY_CUDA(cudaEventRecord(h->ev_early_in, cs));
-    TRY_ST(enqueue_tc_phased(h, buf, D, s, h->ev_late_in, h->ev_early_in));
+    TRY_ST(enqueue_tc_phased(h, buf, D, s, h->ev_in));
   }
   TRY_CUDA(cudaMemcpyAsync(idx_h, idx_d, (size_t)M * k * sizeof(int32_t),
                            cudaMemcpyDeviceToHost, s));

@@ -57,9 +57,9 @@ def test_host_entry_rejects_bad_shapes_without_work(tk):
 
 
 def test_host_entry_equals_device_entry_75y(tk):
-    """The 75-year workload through host buffers takes the two-phase sequence (the
-    later days' strips run while the earlier days are copied in): its results equal
-    the device entry point's bit for bit."""
+    """The 75-year workload through host buffers takes the phased sequence (the strips of
+    the last 35 % of the days run while the earlier days are copied in): its results
+    equal the device entry point's bit for bit."""
     import torch
     X, meta, cfg = config_inputs("euro_75y_46x81")
     L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
@@ -83,3 +83,24 @@ def test_host_entry_with_grid_weights(tk):
     for a, b in zip(hres, dres):
         assert np.array_equal(a.numpy(), b.cpu().numpy())
     h.close()
+
+
+@pytest.mark.parametrize("N,h,w,L,k,e,weights", [(9000, 12, 20, 5, 10, 4, False),
+                                                  (8000, 8, 12, 17, 32, 16, False),
+                                                  (12000, 10, 16, 3, 20, 2, True)])
+def test_host_entry_phases_equal_device_entry(tk, N, h, w, L, k, e, weights):
+    """Series long enough to be split into phases (first phase: the strips of the last
+    35 % of the days, at least the 4,096 days the centring mean reads): bitwise equal to
+    the device entry point, with and without grid-point weights and at the longest L."""
+    import torch
+    X, _ = make_slp_like(N, h, w, seed=N + L)
+    hd = tk.Handle()
+    if weights:
+        hd.set_grid_weights(torch.linspace(0.3, 1.0, h * w, device="cuda"))
+    hres = tk.knn_scores_host(torch.from_numpy(X).pin_memory(), L, k, e, handle=hd)
+    dres = tk.knn_scores(torch.from_numpy(X).cuda(), L, k, e, handle=hd)
+    torch.cuda.synchronize()
+    assert hd.sync_status() == 0
+    for a, b in zip(hres, dres):
+        assert np.array_equal(a.numpy(), b.cpu().numpy())
+    hd.close()
