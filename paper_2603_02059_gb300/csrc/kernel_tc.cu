@@ -221,6 +221,7 @@ __device__ __forceinline__ float kth_of(const RegList<K>& l, int k) {
 }
 
 constexpr int kQueue = 4;  // depth of the per-CTA unit queue
+constexpr size_t kGroupBoundBytes = 2 * BM * 8;  // two groups' tagged row bounds
 
 template <int K, int G>
 __global__ void __launch_bounds__(kThreadsG(G), 1)
@@ -242,7 +243,12 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
   unsigned char* gptr = smem_raw + (ring - raw) + (size_t)NS * p.stage_bytes;
   // epilogue regions (one per group), sized for the largest L and k of the call
   const size_t gbytes = group_bytes(a.kmax, a.Lmax);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gptr + G * gbytes);
+  // two groups: each row's current list bound in each group, tagged with the unit
+  // (the other group's bound also bounds the row's k-th distance; see the scan)
+  volatile unsigned long long* gbound =
+      reinterpret_cast<volatile unsigned long long*>(gptr + G * gbytes);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(gptr + G * gbytes + (G == 2 ? kGroupBoundBytes : 0));
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = full0 + 8u * NS;
   const uint32_t tfull0 = empty0 + 8u * NS;
@@ -283,6 +289,8 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
     ptx::tmem_relinquish();
     ptx::tc_fence_before();
   }
+  if (G == 2)  // no unit has tag 0xFFFFFFFF: every entry starts unused
+    for (int i = threadIdx.x; i < 2 * BM; i += blockDim.x) gbound[i] = ~0ull;
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
@@ -694,6 +702,7 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
                                                 bit_range(xfirst, 32)
                                           : 0u;
           uint32_t cand = 0, ccand = 0;
+          float othr = CUDART_INF_F;  // the other group's bound for this row (two groups)
           if (row_ok) {
             // output column x of this chunk is j = j0 + x; its window is the diagonal
             // Gbuf[l+m][x+m], m < L (Eq. 2 as W_t + W_j - 2 sum G)
@@ -714,8 +723,15 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
             const float lthr = list.threshold();
             // a row candidate has D < lthr and D <= thr_row, i.e. D <= rthr (the float
             // below lthr when lthr > 0; none when lthr is 0)
-            const float rthr =
+            // with two groups, the other group's list for this row in this unit holds K
+            // real candidates of other columns: its K-th bounds the row's k-th too
+            if (G == 2) {
+              const unsigned long long ob = gbound[(1 - gid) * BM + l];
+              if ((unsigned)(ob >> 32) == (unsigned)u) othr = __uint_as_float((unsigned)ob);
+            }
+            float rthr =
                 fminf(lthr > 0.f ? __uint_as_float(__float_as_uint(lthr) - 1u) : -1.f, thr_row);
+            if (G == 2) rthr = fminf(rthr, othr);
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
               c[x] = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);  // D(t, j0 + x)
@@ -753,11 +769,14 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
             const int x = __ffs(cand) - 1;
             cand &= cand - 1;
             const float dv = Gbuf[l * LDG + x];
-            if (dv < list.threshold() && dv <= thr_row) {
+            if (dv < list.threshold() && dv <= thr_row && (G == 1 || dv <= othr)) {
               list.insert(dv, j0 + x);
               ++cnt[0];
             }
           }
+          if (G == 2 && row_ok)
+            gbound[gid * BM + l] =
+                ((unsigned long long)(unsigned)u << 32) | __float_as_uint(list.threshold());
           // column side, written by the rows themselves: column x's list holds its
           // candidate rows in row order (slot = number of candidate rows before
           // this one), unless more than k rows qualify, in which case the column's
@@ -934,7 +953,8 @@ bool make_map(CUtensorMap* m, const void* base, int N, int Dp, int box_rows) {
 }
 
 size_t epilogue_bytes(int k, int L, int G) {
-  return G * group_bytes(k, L) + 8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
+  return G * group_bytes(k, L) + (G == 2 ? kGroupBoundBytes : 0) +
+         8 * (2 * kMaxStages + 5 + 2 * kQueue) + 8 + 4 * kQueue + 16;
 }
 
 int pick_stages(bool split, int k, int L, int G) {
