@@ -176,7 +176,7 @@ inline int list_pitch(int kmax) { return (kmax + 3) / 4 * 4; }
 // (smallest L, most trajectories) defines the units' column ranges.
 void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, int tiles,
                 int group_opt, bool shared, int part_lo, int part_hi,
-                const std::vector<int>& pstrip, int egroups, TcPlan& p) {
+                const std::vector<int>& pstrip, int egroups, int band_tiles, TcPlan& p) {
   p.units.clear();
   p.col_off.clear();
   p.slot_lo.clear();
@@ -242,8 +242,9 @@ void build_plan(const HostSeries* sd, int B, int64_t D, int sym, int cols_opt, i
             if (jlo < jhi) mainq[phase_of(s)].push_back(WorkUnit{b, s, jlo, jhi, c, {nser, 0, 0}});
           }
       }
-      // band: two tiles of columns (2 kTileCols - (L-1) outputs) centred on the strip's rows
-      const int bw = std::max(0, (2 * kTileCols - (Lg - 1) - R) / 2);
+      // band: band_tiles tiles of columns (band_tiles kTileCols - (L-1) outputs) centred on
+      // the strip's rows
+      const int bw = std::max(0, (band_tiles * kTileCols - (Lg - 1) - R) / 2);
       for (int s = std::max(0, part_lo); s < std::min(strips, part_hi); ++s) {
         const int T0 = s * R;
         int jlo = std::max(0, T0 - bw);
@@ -383,10 +384,17 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
                           ? 2
                           : 1;
   key.push_back(egroups);
+  // Band pre-pass width: two tiles per strip when the contraction dominates a tile's
+  // cost; with short operand rows (small grids) a tile's contraction is cheap and the
+  // epilogue decides, and eight tiles give bounds tight enough to save more list
+  // inserts in the main pass than the band costs (D = 32, L = 5: 1.91 -> 1.69 ms; at
+  // D = 3,726 four tiles already cost 6 %)
+  const int band_tiles = tc_groups((int)D * emb) * 64 <= 768 ? 8 : 2;
+  key.push_back(band_tiles);
   TcPlan& p = h->plan;
   if (p.key != key) {
     build_plan(sd, B, D, h->sym, h->unit_cols, tiles, group, shared, part_lo, part_hi, pstrip,
-               egroups, p);
+               egroups, band_tiles, p);
     p.key = key;
     p.emb = emb;
     p.part_lo = part_lo;
