@@ -712,9 +712,12 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
   if (!shared && emb == 1 && whole) TRY_ST(pick_shape(h, sd, B, D, s, &tiles, &group));
   // short operand rows (small grids): the epilogue sets the pace, and units of 16 tiles
   // keep fewer partial lists per row, so fewer list inserts (D = 32, L = 5, embedded:
-  // 1.70 -> 1.61 ms; longer units lose more at the launch's tail than they save)
-  if (tiles == 8 && !h->autotune && tc_groups((int)D * emb) * 64 <= 768)
+  // 1.70 -> 1.61 ms; longer units lose more at the launch's tail than they save), with
+  // 38 strips side by side (1.61 -> 1.58 ms)
+  if (tiles == 8 && !h->autotune && tc_groups((int)D * emb) * 64 <= 768) {
     tiles = 16;
+    if (group == 0 && h->group_strips == 0) group = 38;
+  }
   TcBuffers buf;
   TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi, {}, group));
   h->last_tiles = tiles;
