@@ -236,6 +236,13 @@ struct TcArgs {
   int l2_keep_a;       // 1: load the strip operand with an L2 evict-last policy
   float* scratch;      // [CTAs][2][128 x 256] running tile totals (more than one segment)
   int egroups;         // epilogue groups of the tensor-core kernel (1, or 2 at L = 1)
+  // Band pre-pass in one BF16 product (hi only) on split operands: the correction
+  // entries then add +groups c_a c_b, which the epilogue subtracts (corr_neg = 1), and
+  // every distance is raised by band_margin (W_t + W_j), a bound of its error, before
+  // it enters a list, so that the bounds it publishes stay upper bounds. 0 and 0.0f
+  // for every other launch.
+  int corr_neg;
+  float band_margin;
 };
 
 // Bytes of TcArgs::scratch for a launch of `num_ctas` CTAs.

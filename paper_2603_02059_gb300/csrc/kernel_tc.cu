@@ -612,7 +612,11 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
         // operand preparation); it is added back when a chunk is staged, for every
         // accumulator row whose day exists (halo rows feed other rows' windows)
         const int N = us.M + us.L - 1;
-        const float crow = t < N ? (float)a.groups * a.cval[us.row_base + t] : 0.f;
+        // (with one product on split operands the correction entries added
+        // +groups c_a c_b: subtract it instead)
+        const float crow =
+            t < N ? (a.corr_neg ? -(float)a.groups : (float)a.groups) * a.cval[us.row_base + t]
+                  : 0.f;
         const int jsym = us.T0 + us.R;  // column side from here on (sym)
         const long long cbase = w.sym ? us.col_base + w.col_off[us.strip_base + us.strip] : 0;
         if (nser > 1 || it == 0) list.reset();
@@ -732,9 +736,20 @@ __global__ void __launch_bounds__(kThreadsG(G), 1)
             float rthr =
                 fminf(lthr > 0.f ? __uint_as_float(__float_as_uint(lthr) - 1u) : -1.f, thr_row);
             if (G == 2) rthr = fminf(rthr, othr);
+            if (G == 1 && a.band_margin != 0.f) {
+              // one-product band pre-pass (long operand rows only, so one epilogue
+              // group): the distance raised by a bound of its error
+#pragma unroll
+              for (int x = 0; x < 32; ++x)
+                c[x] = fmaf(a.band_margin, Wt + wv[x],
+                            fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f)) * (1.0f + 0x1p-20f);
+            } else {
+#pragma unroll
+              for (int x = 0; x < 32; ++x)
+                c[x] = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);  // D(t, j0 + x)
+            }
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
-              c[x] = fmaxf(fmaf(-2.0f, c[x], Wt + wv[x]), 0.0f);  // D(t, j0 + x)
               cand |= (c[x] <= rthr ? 1u : 0u) << x;
               ccand |= (c[x] <= tv[x] ? 1u : 0u) << x;
             }

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -427,6 +428,28 @@ traknn_status prepare_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   return TRAKNN_OK;
 }
 
+// The band pre-pass only seeds upper bounds of the rows' k-th distances, from whatever
+// candidates it holds. For split-BF16 calls with long operand rows (more than 768 K
+// entries, where the contraction sets a tile's cost) it runs in one BF16 product (hi
+// only: a third of its tensor work) and raises every distance by a bound of that
+// product's error before it enters a list. For operands a, b (hi = bf16(x), unit
+// roundoff u = 2^-8): |a.b - hi_a.hi_b| <= (2u + u^2) ||a|| ||b||; the FP32
+// accumulation of Dp products and correction terms (sum of magnitudes at most about
+// 2 ||a|| ||b||) adds at most 2.1 Dp 2^-23 ||a|| ||b||, allowing for truncating adds;
+// so each day pair's distance n_a + n_b - 2 G moves by at most
+// (2u + u^2 + 2.1 Dp 2^-23) (n_a + n_b), and a window's by that times W_t + W_j, plus
+// a few FP32 roundings of the epilogue (2^-19). The k-th of the raised distances is
+// then an upper bound of the row's exact k-th distance.
+// (One epilogue group only: the kernel with two groups, which short operand rows use,
+// has no raised-distance path.)
+bool band_single_product(const traknn_ctx* h, const TcPlan& p, int Dp) {
+  return h->precision == TRAKNN_PREC_SPLIT_BF16 && Dp > 768 && p.egroups == 1;
+}
+float band_error_margin(int Dp) {
+  const double u = 1.0 / 256.0;
+  return (float)(2.0 * u + u * u + 2.1 * Dp * std::ldexp(1.0, -23) + std::ldexp(1.0, -19));
+}
+
 // The launch sequence of one tensor-core call (also what a graph captures).
 traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
                          cudaStream_t s, bool record_events) {
@@ -454,6 +477,8 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
   a.cval = b.cval;
   a.l2_keep_a = h->l2_keep_a;
   a.egroups = p.egroups;
+  a.corr_neg = 0;
+  a.band_margin = 0.f;
 
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
@@ -495,7 +520,13 @@ traknn_status enqueue_tc(traknn_ctx* h, const TcBuffers& b, int64_t D,
     bw.sym = 0;
     bw.write_lists = 0;
     bw.counter = w.counter + 1;
-    TRY_CUDA(launch_fused_tc(b.hi, b.lo, split, a, bw, sr, h->sm_count, s));
+    TcArgs ab = a;
+    const bool one = band_single_product(h, p, b.Dp);
+    if (one) {
+      ab.corr_neg = 1;
+      ab.band_margin = band_error_margin(b.Dp);
+    }
+    TRY_CUDA(launch_fused_tc(b.hi, b.lo, one ? false : split, ab, bw, sr, h->sm_count, s));
   }
   TRY_CUDA(launch_fused_tc(b.hi, b.lo, split, a, w, sr, h->sm_count, s));
   if (record_events) {
@@ -570,6 +601,8 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
   a.cval = b.cval;
   a.l2_keep_a = h->l2_keep_a;
   a.egroups = p.egroups;
+  a.corr_neg = 0;
+  a.band_margin = 0.f;
   TcWork w;
   w.units = reinterpret_cast<const WorkUnit*>(pd);
   w.kstride = list_pitch(p.kmax);
@@ -593,12 +626,19 @@ traknn_status enqueue_tc_phased(traknn_ctx* h, const TcBuffers& b, int64_t D, cu
     x.units = w.units + u0;
     x.nunits = nu;
     x.counter = b.counter + ctr;
+    TcArgs ax = a;
+    bool sp = split;
     if (band) {
       x.sym = 0;
       x.write_lists = 0;
+      if (band_single_product(h, p, b.Dp)) {  // see band_error_margin
+        ax.corr_neg = 1;
+        ax.band_margin = band_error_margin(b.Dp);
+        sp = false;
+      }
     }
     ++h->launches;
-    return launch_fused_tc(b.hi, b.lo, split, a, x, sr, h->sm_count, s);
+    return launch_fused_tc(b.hi, b.lo, sp, ax, x, sr, h->sm_count, s);
   };
   for (int q = 0; q < K; ++q) {
     const int lo = p.pstrip[q + 1] * R;                      // first day (and row) of phase q

@@ -67,6 +67,25 @@ def test_shapes_split(tk, N, h, w, L, k, e, embed):
     check_full(X, L, k, e, idx, dist, score, TOL["split_bf16"])
 
 
+@pytest.mark.parametrize("epi_groups", [0, 1])
+def test_single_day_trajectories_on_long_rows(tk, epi_groups):
+    """L = 1 with long operand rows (D = 1,200: 1,280 K entries, one accumulation
+    segment): by default two epilogue groups with the split band pre-pass; with one
+    group the band pre-pass runs in one BF16 product and raises its distances by their
+    error bound before they become row bounds. Full parity with the oracle either way."""
+    import torch
+    X, _ = make_slp_like(1500, 30, 40, seed=1201)
+    L, k, e = 1, 10, 0
+    h = tk.Handle()
+    h.set_option("epi_groups", epi_groups)
+    idx, dist, score = tk.knn_scores(torch.from_numpy(X).cuda(), L, k, e, handle=h)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    h.close()
+    check_full(X, L, k, e, idx.cpu().numpy(), dist.cpu().numpy(), score.cpu().numpy(),
+               TOL["split_bf16"])
+
+
 def test_bf16_error_is_bounded(tk):
     X, meta, cfg = config_inputs("small_5y_16x32")
     L, k, e = cfg["L"], cfg["k"], cfg["exclusion"]
