@@ -20,8 +20,8 @@ namespace {
 // the full mean to shrink the Gram values as well, costs a small fraction of a pass
 // over X, and lies in the first part of X a host-buffer call copies in.
 
-// Column sums of the sampled days over fixed slices (fixed summation order:
-// deterministic).
+// Column sums of the centring days (the last kMeanDays) over fixed slices (fixed
+// summation order: deterministic).
 __global__ void col_partial_kernel(const float* __restrict__ X, int N, int D, float* partial) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D) return;
@@ -91,7 +91,7 @@ __device__ __forceinline__ int find_series(const SeriesInfo* sr, int ns, int r, 
   return lo;
 }
 
-// Column sums of every series' sampled days over fixed slices (grid.z = series).
+// Column sums of every series' centring days over fixed slices (grid.z = series).
 __global__ void col_partial_series_kernel(const __grid_constant__ SeriesTable st, int D,
                                           float* partial) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
