@@ -741,6 +741,36 @@ traknn_status pick_shape(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   return TRAKNN_OK;
 }
 
+// Work-unit shape when neither the autotuner nor an option sets it: Gram tiles per
+// unit and row strips side by side (0 = the planner's default). Short operand rows
+// (small grids): the epilogue sets the pace, and units of 16 tiles keep fewer partial
+// lists per row, so fewer list inserts (D = 32, L = 5, embedded: 1.70 -> 1.61 ms;
+// longer units lose more at the launch's tail than they save), with 38 strips side by
+// side (1.61 -> 1.58 ms). Otherwise the unit length follows the Gram tiles each SM
+// runs (strips [part_lo, part_hi) of every series): eight tiles from 64 tiles per SM
+// (the 75-year series has 78), else shorter units, so that the persistent CTAs run
+// out of work together: four from 16 tiles per SM, two below (L = 5, D = 3,726:
+// N = 10,957 1.31 -> 1.21 ms with two; N = 13,697 1.87 -> 1.83 ms and N = 20,546
+// 3.84 -> 3.72 ms with four; at N = 27,394 the three lengths time alike).
+void default_shape(const traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int emb,
+                   int part_lo, int part_hi, int* tiles, int* group) {
+  if (tc_groups((int)D * emb) * 64 <= 768) {
+    *tiles = 16;
+    if (*group == 0 && h->group_strips == 0) *group = 38;
+    return;
+  }
+  double t = 0.0;  // Gram tiles of the call
+  for (int b = 0; b < B; ++b) {
+    const int64_t M = sd[b].N - sd[b].L + 1;
+    const int R = emb > 1 ? kTileRows : kTileRows - (sd[b].L - 1);
+    const int strips = (int)((M + R - 1) / R);
+    for (int st = std::max(0, part_lo); st < std::min(strips, part_hi); ++st)
+      t += (double)(h->sym ? M - (int64_t)st * R : M) / kTileCols;
+  }
+  const double per_sm = t / std::max(1, h->sm_count);
+  *tiles = per_sm >= 64.0 ? 8 : per_sm >= 16.0 ? 4 : 2;
+}
+
 // Forward pass of B series on the tensor cores. With `graph` set the launch
 // sequence is captured once per (shape, pointers, options) and replayed.
 traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cudaStream_t s,
@@ -750,14 +780,7 @@ traknn_status run_tc(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, cuda
   int tiles = 8, group = 0;
   const bool whole = part_lo == 0 && part_hi == INT_MAX;
   if (!shared && emb == 1 && whole) TRY_ST(pick_shape(h, sd, B, D, s, &tiles, &group));
-  // short operand rows (small grids): the epilogue sets the pace, and units of 16 tiles
-  // keep fewer partial lists per row, so fewer list inserts (D = 32, L = 5, embedded:
-  // 1.70 -> 1.61 ms; longer units lose more at the launch's tail than they save), with
-  // 38 strips side by side (1.61 -> 1.58 ms)
-  if (tiles == 8 && !h->autotune && tc_groups((int)D * emb) * 64 <= 768) {
-    tiles = 16;
-    if (group == 0 && h->group_strips == 0) group = 38;
-  }
+  if (!h->autotune && !shared) default_shape(h, sd, B, D, emb, part_lo, part_hi, &tiles, &group);
   TcBuffers buf;
   TRY_ST(prepare_tc(h, sd, B, D, tiles, shared, emb, s, &buf, part_lo, part_hi, {}, group));
   h->last_tiles = tiles;
@@ -1174,8 +1197,10 @@ traknn_status traknn_knn_scores_host(traknn_handle h, const float* Xh, int64_t N
         TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     const HostSeries sd{Xd, N, L, k, e, idx_d, dist_d, score_d};
+    int tiles = 8, group = 0;
+    default_shape(h, &sd, 1, D, 1, 0, INT_MAX, &tiles, &group);
     TcBuffers buf;
-    TRY_ST(prepare_tc(h, &sd, 1, D, 8, false, 1, s, &buf, 0, INT_MAX, ps));
+    TRY_ST(prepare_tc(h, &sd, 1, D, tiles, false, 1, s, &buf, 0, INT_MAX, ps, group));
     const size_t row = (size_t)D * sizeof(float);
     const cudaStream_t cs = h->copy_stream;
     // the staging buffer is rewritten only after earlier work on `stream` is done
