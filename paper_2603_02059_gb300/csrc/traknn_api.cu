@@ -746,12 +746,14 @@ traknn_status pick_shape(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
 // (small grids): the epilogue sets the pace, and units of 16 tiles keep fewer partial
 // lists per row, so fewer list inserts (D = 32, L = 5, embedded: 1.70 -> 1.61 ms;
 // longer units lose more at the launch's tail than they save), with 38 strips side by
-// side (1.61 -> 1.58 ms). Otherwise the unit length follows the Gram tiles each SM
-// runs (strips [part_lo, part_hi) of every series): eight tiles from 64 tiles per SM
-// (the 75-year series has 78), else shorter units, so that the persistent CTAs run
-// out of work together: four from 16 tiles per SM, two below (L = 5, D = 3,726:
+// side (1.61 -> 1.58 ms). Otherwise the unit length follows the Gram tiles per SM of
+// an average series of the call (strips [part_lo, part_hi)): eight tiles from 64
+// (the 75-year series has 78), four from 16, two below (L = 5, D = 3,726:
 // N = 10,957 1.31 -> 1.21 ms with two; N = 13,697 1.87 -> 1.83 ms and N = 20,546
-// 3.84 -> 3.72 ms with four; at N = 27,394 the three lengths time alike).
+// 3.84 -> 3.72 ms with four; at N = 27,394 the three lengths time alike; 64 series of
+// 3,650 to 27,394 days in one call: four tiles 1.04x faster than eight). Shorter
+// units let the persistent CTAs run out of work together and keep more of a
+// series' operand tiles in L2 while its strips run side by side.
 void default_shape(const traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int emb,
                    int part_lo, int part_hi, int* tiles, int* group) {
   if (tc_groups((int)D * emb) * 64 <= 768) {
@@ -767,7 +769,7 @@ void default_shape(const traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
     for (int st = std::max(0, part_lo); st < std::min(strips, part_hi); ++st)
       t += (double)(h->sym ? M - (int64_t)st * R : M) / kTileCols;
   }
-  const double per_sm = t / std::max(1, h->sm_count);
+  const double per_sm = t / B / std::max(1, h->sm_count);
   *tiles = per_sm >= 64.0 ? 8 : per_sm >= 16.0 ? 4 : 2;
 }
 

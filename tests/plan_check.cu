@@ -107,13 +107,18 @@ void check_plan(int B, int64_t N0, int L, int tiles, int group, int egroups, int
   }
 }
 
-void check_shape(int64_t N, int64_t D, int L, int emb, int sym, int want_tiles, int want_group) {
+void check_shape(int64_t N, int64_t D, int L, int emb, int sym, int want_tiles, int want_group,
+                 int B = 1, int64_t N_last = 0) {
   traknn_ctx h;
   h.sm_count = 152;
   h.sym = sym;
-  const HostSeries sd{nullptr, N, L, 20, L - 1, nullptr, nullptr, nullptr};
+  std::vector<HostSeries> sd(B);
+  for (int b = 0; b < B; ++b) {  // B series, lengths spread evenly from N to N_last
+    const int64_t Nb = B > 1 ? N + (N_last - N) * b / (B - 1) : N;
+    sd[b] = HostSeries{nullptr, Nb, L, 20, L - 1, nullptr, nullptr, nullptr};
+  }
   int tiles = 8, group = 0;
-  default_shape(&h, &sd, 1, D, emb, 0, INT_MAX, &tiles, &group);
+  default_shape(&h, sd.data(), B, D, emb, 0, INT_MAX, &tiles, &group);
   if (tiles != want_tiles || group != want_group) fail("default unit shape", tiles, group);
 }
 
@@ -146,6 +151,10 @@ int main() {
   check_shape(10957, 3726, 5, 1, 1, 2, 0);
   check_shape(10957, 3726, 5, 1, 0, 4, 0);  // both triangles: twice the tiles
   check_shape(27394, 32, 5, 5, 1, 16, 38);
+  // several series: the average series decides
+  check_shape(27394, 3726, 5, 1, 1, 8, 0, 4, 27394);
+  check_shape(3650, 3726, 5, 1, 1, 4, 0, 64, 27394);
+  check_shape(3650, 3726, 5, 1, 1, 2, 0, 8, 9000);
   std::printf("%s\n", g_fail ? "plan check failed" : "plan check ok");
   return g_fail ? 1 : 0;
 }
