@@ -493,7 +493,7 @@ def suite_batched(args):
     ms_seq = _events_ms(seq, args.steps, 3)
     ms_bat = _events_ms(bat, args.steps, 3)
     tiles, group = h.work_shape()
-    # the same batched call with the default work-unit shape (8 tiles, 19 strips)
+    # the same batched call with the default work-unit shape (no autotuning)
     h.set_option("autotune", 0)
     ms_def = _events_ms(lambda: tk.knn_scores_batched(series, handle=h, outs=outs),
                         args.steps, 3)
@@ -510,8 +510,8 @@ def suite_batched(args):
 
 def suite_adjoint(args):
     """30-year workload (N = 10,957, D = 3,726, L = 5, k = 10): forward pass and the
-    adjoint of the summed score; the adjoint is HBM-bound (bytes: read X, idx, g;
-    write dX)."""
+    adjoint of the summed score. The adjoint's floor is its HBM bytes (read X, idx, g;
+    write dX), the fraction reported; its partner-row gather runs from L2."""
     import torch
 
     import paper_2603_02059_gb300 as tk
