@@ -753,7 +753,11 @@ traknn_status pick_shape(traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
 // 3.84 -> 3.72 ms with four; at N = 27,394 the three lengths time alike; 64 series of
 // 3,650 to 27,394 days in one call: four tiles 1.04x faster than eight). Shorter
 // units let the persistent CTAs run out of work together and keep more of a
-// series' operand tiles in L2 while its strips run side by side.
+// series' operand tiles in L2 while its strips run side by side. Long operand rows
+// make every tile long too, so a unit also holds at most 65,536 K entries x tiles
+// (Dp x tiles), two tiles at least: at the 0.25-degree grid (Dp = 59,072, N = 27,394,
+// L = 5) 8 / 4 / 2 tiles took 106.0-108.8 / 99.8-100.7 / 98.9-99.9 ms, while at
+// Dp = 3,840 eight tiles stay within the cap; between the two the cap is a choice.
 void default_shape(const traknn_ctx* h, const HostSeries* sd, int B, int64_t D, int emb,
                    int part_lo, int part_hi, int* tiles, int* group) {
   if (tc_groups((int)D * emb) * 64 <= 768) {
@@ -771,6 +775,8 @@ void default_shape(const traknn_ctx* h, const HostSeries* sd, int B, int64_t D, 
   }
   const double per_sm = t / B / std::max(1, h->sm_count);
   *tiles = per_sm >= 64.0 ? 8 : per_sm >= 16.0 ? 4 : 2;
+  const int64_t Dp = (int64_t)tc_groups((int)D * emb) * 64;
+  while (*tiles > 2 && *tiles * Dp > 65536) *tiles /= 2;
 }
 
 // Forward pass of B series on the tensor cores. With `graph` set the launch

@@ -151,6 +151,10 @@ int main() {
   check_shape(10957, 3726, 5, 1, 1, 2, 0);
   check_shape(10957, 3726, 5, 1, 0, 4, 0);  // both triangles: twice the tiles
   check_shape(27394, 32, 5, 5, 1, 16, 38);
+  // long operand rows: at most 65,536 K entries x tiles per unit, two tiles at least
+  check_shape(27394, 58101, 5, 1, 1, 2, 0);
+  check_shape(27394, 12000, 5, 1, 1, 4, 0);
+  check_shape(10957, 58101, 5, 1, 1, 2, 0);
   // several series: the average series decides
   check_shape(27394, 3726, 5, 1, 1, 8, 0, 4, 27394);
   check_shape(3650, 3726, 5, 1, 1, 4, 0, 64, 27394);
