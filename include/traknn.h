@@ -82,7 +82,12 @@ typedef enum {
                                         every forward call (read with traknn_profile_read) */
   TRAKNN_OPT_SYMMETRIC = 6,          /* tensor-core paths: 1 evaluates each unordered pair once
                                         (upper triangle, Sec. 3.3), 0 both triangles (default 1) */
-  TRAKNN_OPT_UNIT_COLS = 7,          /* tensor-core paths: output columns per work unit, 0 = auto */
+  TRAKNN_OPT_UNIT_COLS = 7,          /* tensor-core paths: output columns per work unit; 0 = auto:
+                                        units of 2, 4 or 8 Gram tiles of 256 columns, by the Gram
+                                        tiles per SM of an average series of the call (8 from
+                                        64, 4 from 16) and at most 65,536 operand K entries x
+                                        tiles; 16 tiles for operand rows of at most 768 K
+                                        entries (the results are the same) */
   TRAKNN_OPT_STATS = 8,              /* 1: count kernel events (read with traknn_stats_read) */
   TRAKNN_OPT_AUTOTUNE = 9,           /* tensor-core paths: 1 times every work-unit shape of
                                         {4, 8, 16} Gram tiles per unit x {10, 19, 38} row strips
