@@ -136,13 +136,23 @@ int main() {
   check_plan(1, 300, 2, 8, 19, 1, 1, 0, INT_MAX, {}, 2);
   check_plan(1, 20, 2, 8, 19, 1, 1, 0, INT_MAX, {}, 2);     // one partial strip
   check_plan(5, 6000, 3, 4, 19, 1, 1, 0, INT_MAX, {}, 2);   // batched, uneven series
-  for (int64_t N : {9000, 27394}) {
-    const int L = 5, R = kTileRows - (L - 1);
-    const int strips = (int)((N - L + 1 + R - 1) / R);
-    const std::vector<int> ps = phase_plan(strips, R, N);
-    if (ps.empty()) fail("no phases", (int)N, 0);
-    check_plan(1, N, L, 8, 19, 1, 1, 0, INT_MAX, ps, 2);
-  }
+  // host-buffer calls in phases: long series are split; a series is not when it has
+  // fewer than 8 strips or when phase 0 (which holds the last 4,096 days, read by the
+  // centring mean) would take nearly all of it
+  for (int64_t N : {300, 1000, 1100, 3000, 5000, 9000, 15000, 27394})
+    for (int L : {2, 5, 17}) {
+      const int R = kTileRows - (L - 1);
+      const int strips = (int)((N - L + 1 + R - 1) / R);
+      const std::vector<int> ps = phase_plan(strips, R, N);
+      if ((strips < 8 || N <= kMeanDays) && !ps.empty()) fail("phase split", (int)N, L);
+      if (N >= 9000 && ps.empty()) fail("long series not split", (int)N, L);
+      if (!ps.empty()) {
+        if (ps.front() != strips || ps.back() != 0) fail("phase ends", (int)N, L);
+        for (size_t q = 0; q + 1 < ps.size(); ++q)
+          if (ps[q + 1] >= ps[q]) fail("phase order", (int)N, L);
+        for (int tiles : {2, 8}) check_plan(1, N, L, tiles, 19, 1, 1, 0, INT_MAX, ps, 2);
+      }
+    }
   // unit length: 8 tiles at the 75-year length, shorter for shorter series, 16 tiles
   // and 38 strips for short operand rows
   check_shape(27394, 3726, 5, 1, 1, 8, 0);
